@@ -1,0 +1,504 @@
+"""Pins of the CPU oracle against facts other than itself (no GPU needed).
+
+Each test names what fixes the expected value: published known answers,
+Python's exact integer / rational arithmetic, math.fsum (a correctly rounded
+sum), brute-force enumeration, hand-worked examples, closed forms and
+invariants of the method (Alg. 1-3 of the paper).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_09950_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox
+
+def test_philox_known_answers():
+    """Philox4x32-10 against the generator's published known answers."""
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        lhs, rhs = line.split("->")
+        words = [int(x, 16) for x in lhs.split()]
+        expect = [int(x, 16) for x in rhs.split()]
+        got = oracle.philox(words[:4], words[4:6])
+        assert [int(v) for v in got] == expect
+        n += 1
+    assert n == 3
+
+
+def test_fmix32_is_a_bijection_and_avalanches():
+    """MurmurHash3's finaliser is invertible (no collisions on a large sample)
+    and flips about half of the output bits per input bit."""
+    rng = np.random.default_rng(7)
+    xs = np.unique(rng.integers(0, 2**32, size=200_000, dtype=np.uint64))
+    ys = {oracle.fmix32(int(x)) for x in xs[:20000]}
+    assert len(ys) == min(20000, xs.size)
+    flips = []
+    for x in xs[:500]:
+        h = oracle.fmix32(int(x))
+        for b in range(32):
+            flips.append(bin(h ^ oracle.fmix32(int(x) ^ (1 << b))).count("1"))
+    assert abs(np.mean(flips) - 16.0) < 0.5
+    assert oracle.fmix32(0) == 0
+
+
+# ---------------------------------------------------------------- permutations
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 16, 17, 63, 64, 65, 1000, 4097])
+def test_feistel_is_a_permutation(n):
+    """Cycle-walked Feistel network: a bijection of [0, n) for every n."""
+    out = oracle.perm(n, 12345, 1, 2, 3, np.arange(n))
+    assert sorted(out.tolist()) == list(range(n))
+
+
+def test_feistel_positions_are_uniform():
+    """Across many keys, sigma(i) is uniform over [0, n) (chi-square)."""
+    n, keys = 37, 4000
+    counts = np.zeros((n, n))
+    for k in range(keys):
+        s = oracle.perm(n, 99, k, 5, 6, np.arange(n))
+        counts[np.arange(n), s] += 1
+    exp = keys / n
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    dof = (n - 1) * (n - 1)
+    assert abs(chi2 - dof) < 6 * math.sqrt(2 * dof)
+
+
+def test_shadow_columns_are_row_permutations():
+    """Alg. 1: each shadow column holds the values of its source column,
+    shuffled; columns are doubled until there are at least five."""
+    w = synth.binary_small(N=300, p=3, n_inf=1)
+    P = oracle.BorutaProblem(w.X, w.y, **w.params(), N=w.N)
+    live = np.array([0, 2], dtype=np.int32)
+    sha = P.shadow(1, live)
+    assert sha.shape == (oracle.shadow_count(2), 300) == (8, 300)
+    for c in range(sha.shape[0]):
+        src = w.X[live[c % 2], :300]
+        assert np.array_equal(np.sort(sha[c]), np.sort(src))
+        assert not np.array_equal(sha[c], src)
+    assert not np.array_equal(sha[0], sha[2])  # copies get different shuffles
+    assert [oracle.shadow_count(k) for k in (1, 2, 3, 4, 5, 6)] == [8, 8, 6, 8, 5, 6]
+
+
+def test_permut_table_is_a_permutation():
+    w = synth.binary_small(N=777, p=2, n_inf=1)
+    P = oracle.BorutaProblem(w.X, w.y, **w.params(), N=w.N)
+    pi = P.permut_table(3)
+    assert sorted(pi.tolist()) == list(range(777))
+
+
+# ---------------------------------------------------------------- bootstrap, mtry
+
+def test_bootstrap_counts_are_multinomial():
+    """N draws with replacement: counts sum to N, out-of-bag fraction near
+    (1-1/N)^N, count histogram near Poisson(1)."""
+    N = 20000
+    c = oracle.bootstrap(0, 0, 1, 3, N)
+    assert c.sum() == N
+    assert abs((c == 0).mean() - (1 - 1 / N) ** N) < 0.01
+    for k in range(4):
+        pk = math.exp(-1) / math.factorial(k)
+        assert abs((c == k).mean() - pk) < 0.01
+    assert not np.array_equal(c, oracle.bootstrap(0, 0, 1, 4, N))
+
+
+def test_mtry_sample_is_distinct_and_uniform():
+    p_aug, mtry = 40, 6
+    freq = np.zeros(p_aug)
+    for v in range(3000):
+        f = oracle.mtry_features(5, 0, 2, 1, v, p_aug, mtry)
+        assert len(set(f.tolist())) == mtry and f.max() < p_aug
+        freq[f] += 1
+    exp = 3000 * mtry / p_aug
+    assert np.all(np.abs(freq - exp) < 5 * math.sqrt(exp))
+
+
+def test_default_mtry():
+    assert oracle.default_mtry(0, 100) == 10
+    assert oracle.default_mtry(0, 2000) == 44
+    assert oracle.default_mtry(1, 40000) == 13333
+    assert oracle.default_mtry(0, 1000) == 31
+    assert oracle.default_mtry(1, 2) == 1
+
+
+# ---------------------------------------------------------------- exact arithmetic
+
+def test_cmp_products_matches_python_integers():
+    rng = np.random.default_rng(1)
+    for _ in range(3000):
+        bits = rng.integers(1, 128)
+        a1, b1, a2, b2 = (int(rng.integers(0, 2**63)) << int(rng.integers(0, bits)) for _ in range(4))
+        want = (a1 * b1 > a2 * b2) - (a1 * b1 < a2 * b2)
+        if max(a1 * b1, a2 * b2) >= 2**256:
+            want = 2
+        assert oracle.cmp_products(a1, b1, a2, b2) == want
+    assert oracle.cmp_products(2**200, 2**56, 1, 1) == 2  # 2^256 overflows
+
+
+def test_u256_to_double_is_correctly_rounded():
+    """Against Python's int -> float (round half to even)."""
+    cases = [0, 1, 2**53 - 1, 2**53, 2**53 + 1, 2**53 + 2, 2**53 + 3, 2**54 + 2, 2**54 + 6,
+             2**64 - 1, 2**127, 2**127 + 2**74, 2**127 + 2**74 + 1, 2**255 + 1, 2**256 - 1,
+             (2**53 - 1) << 100, ((2**53 - 1) << 100) + (1 << 99)]
+    rng = np.random.default_rng(2)
+    for _ in range(2000):
+        v = int(rng.integers(1, 2**63)) << int(rng.integers(0, 190))
+        v += int(rng.integers(0, 2**63))
+        cases.append(v)
+    for v in cases:
+        assert oracle.u256_to_double(v) == float(v), hex(v)
+
+
+def test_exact_sum_matches_fsum():
+    """math.fsum is a correctly rounded sum of doubles."""
+    rng = np.random.default_rng(3)
+    for trial in range(300):
+        n = int(rng.integers(1, 400))
+        x = rng.standard_normal(n) * np.exp2(rng.integers(-60, 60, size=n))
+        if trial % 3 == 0:  # heavy cancellation
+            x = np.concatenate([x, -x[::-1] * (1 + 2**-40)])
+        assert oracle.exact_sum(x) == math.fsum(x)
+    assert oracle.exact_sum([1e300, 1.0, -1e300]) == 1.0
+    assert oracle.exact_sum([2**-1074, 2**-1074]) == math.fsum([2**-1074, 2**-1074])
+    assert oracle.exact_sum([]) == 0.0
+
+
+@pytest.mark.parametrize("t", [1, 2, 7, 20, 63, 64, 100, 126])
+def test_binomial_tails(t):
+    """Exact tails against math.comb; closed forms and symmetry."""
+    for h in range(0, t + 1):
+        pa, pr, up, lo = oracle.binom_tails(t, h)
+        assert up == sum(math.comb(t, k) for k in range(h, t + 1))
+        assert lo == sum(math.comb(t, k) for k in range(0, h + 1))
+        assert pa == float(Fraction(up, 2**t))  # one correct rounding
+        assert pr == float(Fraction(lo, 2**t))
+        assert oracle.binom_tails(t, t - h)[3] == up  # U(t,h) = L(t,t-h)
+    assert oracle.binom_tails(t, 0)[0] == 1.0
+    assert oracle.binom_tails(t, t)[0] == 2.0**-t
+    assert oracle.binom_tails(t, 0)[1] == 2.0**-t
+
+
+# ---------------------------------------------------------------- split search
+
+def _golden_examples():
+    for line in open(os.path.join(GOLDEN, "gini_worked_examples.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        kind, C, y, x, w, f, b, d = line.strip().split("|")
+        num, den = d.split("/")
+        yield (kind, int(C), [int(v) for v in y.split(",")], [int(v) for v in x.split(",")],
+               [int(v) for v in w.split(",")], int(f), int(b), Fraction(int(num), int(den)))
+
+
+@pytest.mark.parametrize("ex", list(_golden_examples()))
+def test_hand_worked_gains(ex):
+    kind, C, y, x, w, f, b, delta = ex
+    task = 0 if kind == "cls" else 1
+    bins = np.array(x, dtype=np.uint8)[:, None]
+    got = oracle.node_split(task, C, 8, bins, w, y, [0])
+    assert got is not None
+    assert got[0] == f and got[1] == b
+    assert got[2] == pytest.approx(float(delta), rel=1e-15)
+
+
+def _impurity(task, C, ys, ws):
+    """n * impurity from its definition: Gini n(1 - sum p_k^2) or n * Var."""
+    n = sum(ws)
+    if task == 0:
+        return n * (1 - sum(Fraction(sum(w for yy, w in zip(ys, ws) if yy == k), n) ** 2
+                            for k in range(C)))
+    mean = Fraction(sum(w * yy for yy, w in zip(ys, ws)), n)
+    return sum(w * (yy - mean) ** 2 for yy, w in zip(ys, ws))
+
+
+def _brute_force(task, C, B, bins, w, y, feats):
+    bins = np.asarray(bins).tolist()  # exact Python integers from here on
+    w = [int(v) for v in w]
+    y = [int(v) for v in y]
+    feats = [int(f) for f in feats]
+    rows = range(len(bins))
+    n_par = _impurity(task, C, list(y), list(w))
+    best = None
+    for f in feats:
+        for b in range(B - 1):
+            L = [r for r in rows if bins[r][f] <= b]
+            R = [r for r in rows if bins[r][f] > b]
+            if sum(w[r] for r in L) == 0 or sum(w[r] for r in R) == 0:
+                continue
+            d = (n_par - _impurity(task, C, [y[r] for r in L], [w[r] for r in L])
+                 - _impurity(task, C, [y[r] for r in R], [w[r] for r in R]))
+            if best is None or d > best[2]:
+                best = (f, b, d)
+    if best is None or best[2] <= 0:
+        return None
+    return best
+
+
+@pytest.mark.parametrize("task", [0, 1])
+def test_split_search_matches_brute_force(task):
+    """Exhaustive enumeration with exact fractions of the impurity-decrease
+    definition (a different formula from the oracle's integer form)."""
+    rng = np.random.default_rng(11 + task)
+    for _ in range(250):
+        nrows = int(rng.integers(1, 13))
+        nf = int(rng.integers(1, 5))
+        B = int(rng.integers(2, 9))
+        C = int(rng.integers(2, 5)) if task == 0 else 1
+        bins = rng.integers(0, B, size=(nrows, nf)).astype(np.uint8)
+        w = rng.integers(1, 4, size=nrows)
+        y = rng.integers(0, C, size=nrows) if task == 0 else rng.integers(-50, 50, size=nrows)
+        feats = rng.permutation(nf)[: int(rng.integers(1, nf + 1))]
+        want = _brute_force(task, C, B, bins, w, y, feats)
+        got = oracle.node_split(task, C, B, bins, w, y, feats)
+        if want is None:
+            assert got is None
+        else:
+            assert got is not None and got[:2] == want[:2]
+            assert got[2] == pytest.approx(float(want[2]), rel=1e-15)
+
+
+# ---------------------------------------------------------------- trees
+
+def _small(importance=0, **kw):
+    args = dict(N=400, p=12, n_inf=3, n_trees=5, max_depth=6, max_iter=3)
+    args.update(kw)
+    w = synth.binary_small(importance=importance, **args)
+    return w, oracle.BorutaProblem(w.X, w.y, **w.params(), N=w.N)
+
+
+def _naive_tree(P, t, live, Xsha, tree, w):
+    """Second, naive recursive tree builder: bootstrap and feature sample from
+    the (separately pinned) streams, splits from exact-fraction brute force."""
+    N = P.N
+    cols = np.concatenate([P.X[live, :N], Xsha], axis=0)
+    p_aug = cols.shape[0]
+    cnt = oracle.bootstrap(P.c.seed, 0, t, tree, N)
+    mtry = oracle.default_mtry(0, p_aug)
+    out = []
+
+    def grow(rows, heap, depth):
+        ws = cnt[rows]
+        ys = P.y[rows]
+        node = dict(heap=heap, depth=depth, feature=-1, bin=0, n_rows=len(rows), n=int(ws.sum()))
+        out.append(node)
+        if depth >= P.c.max_depth:
+            return
+        feats = oracle.mtry_features(P.c.seed, 0, t, tree, heap, p_aug, mtry)
+        best = _brute_force(0, P.n_classes, P.c.n_bins, cols[:, rows].T, ws, ys, feats)
+        if best is None:
+            return
+        f, b, _ = best
+        node["feature"], node["bin"] = int(f), int(b)
+        grow(rows[cols[f, rows] <= b], 2 * heap + 1, depth + 1)
+        grow(rows[cols[f, rows] > b], 2 * heap + 2, depth + 1)
+
+    grow(np.flatnonzero(cnt > 0), 0, 0)
+    return sorted(out, key=lambda d: (d["depth"], d["heap"]))
+
+
+def test_tree_rebuilds_from_naive_builder():
+    w, P = _small(N=120, p=5, max_depth=4)
+    live = np.arange(5, dtype=np.int32)
+    sha = P.shadow(1, live)
+    for tree in range(2):
+        nodes, _, _ = P.tree(1, live, sha, tree)
+        naive = _naive_tree(P, 1, live, sha, tree, w)
+        assert len(nodes) == len(naive)
+        for a, b in zip(nodes, naive):
+            for k in ("heap", "depth", "feature", "bin", "n_rows", "n"):
+                assert int(a[k]) == b[k], (k, a, b)
+
+
+def test_tree_structure_invariants():
+    w, P = _small(N=600, p=20, max_depth=7)
+    live = np.arange(20, dtype=np.int32)
+    sha = P.shadow(2, live)
+    nodes, _, _ = P.tree(2, live, sha, 0)
+    by_heap = {int(n["heap"]): n for n in nodes}
+    for n in nodes:
+        assert n["depth"] <= 7
+        assert n["stat"][:2].sum() == n["n"]
+        if n["feature"] >= 0:
+            L, R = by_heap[2 * int(n["heap"]) + 1], by_heap[2 * int(n["heap"]) + 2]
+            assert L["n"] + R["n"] == n["n"] and L["n_rows"] + R["n_rows"] == n["n_rows"]
+            assert np.array_equal(L["stat"] + R["stat"], n["stat"])
+            assert n["delta"] > 0
+        else:
+            assert 2 * int(n["heap"]) + 1 not in by_heap
+    root = by_heap[0]
+    assert root["n"] == 600  # N bootstrap draws
+
+
+def test_treeimp_invariants():
+    """Alg. 2: per-tree rows sum to 1 (or are all 0); features never split
+    on get exactly 0; a depth-1 tree puts everything on its root feature."""
+    w, P = _small(N=500, p=15, max_depth=5)
+    live = np.arange(15, dtype=np.int32)
+    sha = P.shadow(1, live)
+    for tree in range(3):
+        nodes, ti, _ = P.tree(1, live, sha, tree, treeimp=True)
+        assert ti.sum() == pytest.approx(1.0, abs=1e-14)
+        used = set(int(f) for f in nodes["feature"] if f >= 0)
+        for j in range(ti.size):
+            if j not in used:
+                assert ti[j] == 0.0
+            else:
+                assert ti[j] > 0.0
+    w1, P1 = _small(N=500, p=15, max_depth=1)
+    nodes, ti, _ = P1.tree(1, live, P1.shadow(1, live), 0, treeimp=True)
+    assert ti[nodes["feature"][0]] == 1.0 and ti.sum() == 1.0
+
+
+def test_treeimp_matches_alg2_recursion():
+    """Alg. 2 literally: CalcNodeImp recursion in float, normalised by the
+    per-tree total -- equal to the oracle's exact sums up to rounding."""
+    w, P = _small(N=500, p=15, max_depth=6)
+    live = np.arange(15, dtype=np.int32)
+    sha = P.shadow(1, live)
+    nodes, ti, _ = P.tree(1, live, sha, 1, treeimp=True)
+    by_heap = {int(n["heap"]): n for n in nodes}
+    gains = np.zeros(ti.size)
+
+    def calc(v):
+        n = by_heap[v]
+        if n["feature"] < 0:
+            return
+        gains[n["feature"]] += n["delta"]
+        calc(2 * v + 1)
+        calc(2 * v + 2)
+
+    calc(0)
+    np.testing.assert_allclose(ti, gains / gains.sum(), rtol=1e-13, atol=1e-16)
+
+
+def test_permut_invariants_and_stump_closed_form():
+    """Alg. 3 on out-of-bag rows: exactly 0 for features not on any path; for a
+    stump, the importance of the root feature is the mean over OOB rows of
+    the loss between the two leaves, counted over rows whose permuted value
+    crosses the threshold -- computed here from the raw data."""
+    w, P = _small(importance=2, N=500, p=15, max_depth=4)
+    live = np.arange(15, dtype=np.int32)
+    sha = P.shadow(1, live)
+    nodes, _, pm = P.tree(1, live, sha, 0, permut=True)
+    used = set(int(f) for f in nodes["feature"] if f >= 0)
+    for j in range(pm.size):
+        if j not in used:
+            assert pm[j] == 0.0
+    assert all(pm[j] >= 0 for j in used)
+
+    w1, P1 = _small(importance=2, N=500, p=15, max_depth=1)
+    sha = P1.shadow(1, live)
+    nodes, _, pm = P1.tree(1, live, sha, 2, permut=True)
+    root, L, R = nodes[0], nodes[1], nodes[2]
+    f, b = int(root["feature"]), int(root["bin"])
+    col = np.concatenate([w1.X[live, :500], sha])[f]
+    pi = P1.permut_table(1)
+    oob = np.flatnonzero(oracle.bootstrap(0, 0, 1, 2, 500) == 0)
+    eps = 1e-7
+
+    def probs(n):
+        return (n["stat"][:2] / n["n"] + eps) / (1 + 2 * eps)
+
+    def kl(a, c):
+        pa, pc = probs(a), probs(c)
+        return float(np.sum(pa * np.log(pa / pc)))
+
+    total = 0.0
+    for i in oob:
+        q = L if col[i] <= b else R
+        q2 = L if col[pi[i]] <= b else R
+        if q is not q2:
+            total += kl(q, q2)
+    assert pm[f] == pytest.approx(total / oob.size, rel=1e-12)
+    assert np.count_nonzero(pm) <= 1
+
+
+def test_permut_constant_column_is_zero():
+    """Swapping in values of a constant column changes no prediction."""
+    w, P = _small(importance=2, N=300, p=6, max_depth=5)
+    X = w.X.copy()
+    X[2, :] = 7
+    P2 = oracle.BorutaProblem(X, w.y, **w.params(), N=w.N)
+    live = np.arange(6, dtype=np.int32)
+    sha = P2.shadow(1, live)
+    _, _, pm = P2.tree(1, live, sha, 0, permut=True)
+    assert pm[2] == 0.0
+
+
+# ---------------------------------------------------------------- statistics
+
+def test_zscore_closed_forms():
+    """One tree: sd = 0, so Z is 0 for zero mean and +inf otherwise; with the
+    mean statistic, s is the single tree's importance row."""
+    w, P = _small(N=300, p=8, n_trees=1, max_iter=1)
+    out = P.iteration(1, np.zeros(8, np.int8), np.zeros(8, np.int32))
+    imp = out["imp"][0]
+    assert np.all(out["s"][imp == 0] == 0.0) and np.all(np.isinf(out["s"][imp > 0]))
+    w2, P2 = _small(N=300, p=8, n_trees=1, max_iter=1, )
+    P2.c.stat = 1
+    out2 = P2.iteration(1, np.zeros(8, np.int8), np.zeros(8, np.int32))
+    np.testing.assert_array_equal(out2["s"], out2["imp"][0])
+
+
+def test_iteration_statistics_from_importance_rows():
+    """Mean, sd (M-1), Z, shadow max and hits recomputed from the dumped
+    importance matrix with exactly rounded sums (math.fsum)."""
+    w, P = _small(N=400, p=10, n_trees=7, max_iter=1)
+    state = np.zeros(10, np.int8)
+    state[3] = -1
+    state[5] = 1
+    out = P.iteration(1, state, np.zeros(10, np.int32))
+    imp, s = out["imp"], out["s"]
+    M = imp.shape[0]
+    live = np.flatnonzero(state >= 0)
+    for j in range(imp.shape[1]):
+        mean = math.fsum(imp[:, j]) / M
+        sd = math.sqrt(math.fsum([(v - mean) * (v - mean) for v in imp[:, j]]) / (M - 1))
+        z = (0.0 if mean == 0 else math.inf) if sd == 0 else mean / (sd / math.sqrt(M))
+        assert s[j] == z
+    smax = s[live.size:].max()
+    assert out["shadow_max"] == smax
+    for a, j in enumerate(live):
+        assert out["hits"][j] == int(s[a] > smax)
+        assert out["hist"][j] == s[a]
+    assert np.isnan(out["hist"][3])
+    assert out["state"][3] == -1 and out["state"][5] == 1
+
+
+def test_decision_thresholds():
+    """Earliest possible decision: accept needs 2^-t < alpha/m, so with
+    alpha = 0.01 and m = 50 undecided features the first accept can come at
+    t = ceil(log2(m/alpha)) = 13 and never before."""
+    m, alpha = 50, 0.01
+    t_min = math.ceil(math.log2(m / alpha))
+    assert t_min == 13
+    assert oracle.binom_tails(t_min, t_min)[0] < alpha / m
+    assert not oracle.binom_tails(t_min - 1, t_min - 1)[0] < alpha / m
+
+
+# ---------------------------------------------------------------- end to end
+
+@pytest.mark.slow
+def test_planted_informative_set_is_found():
+    """Binary N=1000, p=50: exactly the 10 planted class-conditional columns
+    are accepted and every noise column is rejected within 20 iterations;
+    no decision before t = 13."""
+    w = synth.binary_small()
+    P = oracle.BorutaProblem(w.X, w.y, **w.params(), N=w.N)
+    r = P.run()
+    acc = set(np.flatnonzero(r["decision"] == 1).tolist())
+    assert acc == set(w.informative.tolist())
+    assert np.all(r["decision"][np.setdiff1d(np.arange(50), w.informative)] != 1)
+    assert (r["decision"] == -1).sum() >= 36
+    assert r["iterations"] <= 20
+    first = np.isnan(r["imp_history"]).any(axis=1).argmax()
+    assert first == 0 or first >= 13

@@ -1,0 +1,195 @@
+/*
+ * boruta.h -- C ABI of the GB300-native GPU Boruta library.
+ *
+ * The library runs the data-parallel hot path of GPU Boruta (Li et al.,
+ * "Novel GPU Boruta algorithms for feature selection from high-dimensional
+ * data"): every iteration of Alg. 1 -- shadow features, a random forest fit
+ * on the shadow-augmented matrix, per-tree impurity importance (Alg. 2) or
+ * out-of-bag permutation importance (Alg. 3), the hit update and the
+ * Bonferroni-corrected binomial accept/reject test -- as CUDA kernels for
+ * sm_103a.  All entry points use plain pointers and sizes; none takes or
+ * returns a framework type.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: 0 (BORUTA_OK) on success, a negative boruta_status on
+ *     error; boruta_last_error() then returns a message (thread-local).
+ *     On error, caller-owned outputs are left unspecified.
+ *   - Ownership: all pointers are caller-owned.  The library allocates only
+ *     its own device workspace, released before boruta_fit returns or by
+ *     boruta_session_destroy.
+ *   - X is the quantised feature matrix, column-major uint8 bins: column j
+ *     starts at X + j*ld (ld >= N bytes, ld and X 16-byte aligned for the
+ *     vectorised path; other strides are accepted and use a slower path).
+ *     Every bin must be < n_bins.
+ *   - y: classification labels as uint8 in [0, n_classes), or regression
+ *     targets as int64 fixed point in units of 2^-20.
+ *   - Device pointers are accepted unless opts->host_inputs = 1, in which
+ *     case X and y are host pointers copied in by the call.
+ *   - Work is queued on opts->stream (NULL: the legacy default stream); the
+ *     fit calls synchronise that stream once per Boruta iteration.
+ *
+ * Limits (BORUTA_EINVAL beyond them): 1 <= N < 2^24, 1 <= p < 2^23,
+ * 2 <= n_bins <= 256, 1 <= n_classes <= 8, 1 <= n_trees < 2^20,
+ * 0 <= max_depth <= 30, 1 <= max_iter <= 126, 0 < alpha.
+ * Regression targets must satisfy N * max|y| < 2^62 (BORUTA_EOVERFLOW).
+ */
+#ifndef BORUTA_GB300_H
+#define BORUTA_GB300_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BORUTA_OK = 0,
+  BORUTA_EINVAL = -1,    /* bad argument, size or input value */
+  BORUTA_EOVERFLOW = -2, /* an integer bound guard tripped (weights, sums, pools) */
+  BORUTA_ETIMEOUT = -3,  /* a bounded device wait gave up */
+  BORUTA_ECUDA = -4,     /* a CUDA runtime call failed */
+  BORUTA_ENOMEM = -5     /* device workspace allocation failed */
+} boruta_status;
+
+/* task = kind | importance */
+#define BORUTA_CLASSIFICATION 0 /* Gini criterion, KL loss for Alg. 3 */
+#define BORUTA_REGRESSION 1     /* variance criterion, squared-error loss for Alg. 3 */
+#define BORUTA_TREEIMP 0        /* Alg. 2: impurity decrease ("gain x samples") */
+#define BORUTA_PERMUT 2         /* Alg. 3 on each tree's out-of-bag rows */
+
+typedef struct {
+  int stat;        /* hit statistic: 0 = Z score mean/(sd/sqrt(M)) (default), 1 = mean */
+  int precision;   /* per-term arithmetic: 0 = FP64 (default), 1 = FP32; sums are exact either way */
+  int tie_break;   /* equal split scores: 0 = feature drawn first at the node (default), 1 = lowest index */
+  int n_classes;   /* classification: 0 = max(y) + 1 */
+  double kl_eps;   /* class-probability smoothing in the KL loss; default 1e-7 */
+  void* stream;    /* cudaStream_t to run on; NULL = legacy default stream */
+  uint32_t job;    /* job id folded into every random stream (batches); default 0 */
+  int host_inputs; /* 1: X and y are host pointers, copied to the device inside the call */
+  int graph;       /* 1: replay each iteration's level loop as a CUDA graph */
+} boruta_opts;
+
+/* Host-side, caller-allocated outputs. */
+typedef struct {
+  int8_t* decision;    /* [p]: 1 accepted, 0 tentative, -1 rejected */
+  int32_t* hits;       /* [p]: iterations in which the feature beat the best shadow */
+  double* imp_history; /* [max_iter * p]: row t-1 = hit statistic at iteration t, NaN if not in play */
+  double* shadow_max;  /* [max_iter]: best shadow statistic per iteration (NaN after the last) */
+  int32_t iterations;  /* iterations run */
+} boruta_result;
+
+/* Fills opts with the defaults above. */
+void boruta_default_opts(boruta_opts* opts);
+
+/*
+ * boruta_fit -- the whole of Alg. 1 on one problem.
+ *   X        [in]  bins, column-major, column j at X + j*ld (see conventions)
+ *   ld       [in]  column stride in bytes, >= N
+ *   y        [in]  uint8 labels or int64 fixed-point targets, N entries
+ *   N, p     [in]  rows and columns
+ *   task     [in]  kind | importance (BORUTA_CLASSIFICATION/REGRESSION | BORUTA_TREEIMP/PERMUT)
+ *   n_trees  [in]  trees per forest (M)
+ *   max_depth[in]  root has depth 0; nodes at max_depth are leaves
+ *   mtry     [in]  features tried per node; 0 = floor(sqrt(p_aug)) (classification) or
+ *                  floor(p_aug/3) (regression), recomputed as columns are rejected
+ *   n_bins   [in]  number of bins B; split thresholds are bins 0..B-2
+ *   max_iter [in]  t_max of Alg. 1
+ *   alpha    [in]  significance level before Bonferroni correction
+ *   seed     [in]  key of every random stream
+ *   opts     [in]  NULL = defaults
+ *   out      [out] host buffers sized as documented in boruta_result
+ */
+int boruta_fit(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p, int task,
+               int n_trees, int max_depth, int mtry, int n_bins, int max_iter, double alpha,
+               uint64_t seed, const boruta_opts* opts, boruta_result* out);
+
+/*
+ * Step-wise interface: the same computation one Boruta iteration at a time
+ * (Alg. 1 loop body), for benchmarking, checkpoint/resume and inspection.
+ * A session owns its device workspace; X and y must stay valid (device
+ * pointers) until boruta_session_destroy.  Not thread-safe per session.
+ */
+typedef struct boruta_session boruta_session;
+
+int boruta_session_create(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p,
+                          int task, int n_trees, int max_depth, int mtry, int n_bins, int max_iter,
+                          double alpha, uint64_t seed, const boruta_opts* opts,
+                          boruta_session** out);
+
+/* Runs iteration t+1.  *undecided receives the number of undecided features
+ * after its test (0 or t == max_iter: the run is finished; stepping a
+ * finished session returns BORUTA_EINVAL). */
+int boruta_session_step(boruta_session* s, int32_t* undecided);
+
+/* Copies the Boruta state to host buffers (any may be NULL): decision[p],
+ * hits[p], imp_history[max_iter*p], shadow_max[max_iter], *t. */
+int boruta_session_read(boruta_session* s, int8_t* decision, int32_t* hits, double* imp_history,
+                        double* shadow_max, int32_t* t);
+
+/* Restores a state read earlier (resume from a checkpoint): the next step
+ * runs iteration t+1 and reproduces the uninterrupted run exactly. */
+int boruta_session_write(boruta_session* s, const int8_t* decision, const int32_t* hits,
+                         const double* imp_history, const double* shadow_max, int32_t t);
+
+/* Dumps of the last completed iteration, for parity checks.  what:
+ *   BORUTA_DUMP_SHADOW   uint8  [n_sha * N]   shadow columns (Alg. 1 X_sha)
+ *   BORUTA_DUMP_BOOT     uint32 [M * N]       bootstrap draw counts per tree
+ *   BORUTA_DUMP_IMP      double [M * p_aug]   per-tree importance rows
+ *   BORUTA_DUMP_STAT     double [p_aug]       hit statistic per augmented column
+ *   BORUTA_DUMP_NODES    boruta_node [count]  trees in order, each in (depth, heap) order
+ *   BORUTA_DUMP_TREE_PTR int64  [M + 1]       offsets of each tree in the node dump
+ *   BORUTA_DUMP_LIVE     int32  [p_live]      original columns in play
+ * host must hold capacity bytes; *bytes receives the size needed (pass
+ * host = NULL to query).  */
+#define BORUTA_DUMP_SHADOW 1
+#define BORUTA_DUMP_BOOT 2
+#define BORUTA_DUMP_IMP 3
+#define BORUTA_DUMP_STAT 4
+#define BORUTA_DUMP_NODES 5
+#define BORUTA_DUMP_TREE_PTR 6
+#define BORUTA_DUMP_LIVE 7
+int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacity, int64_t* bytes);
+
+/* Timing of the dominant kernel of the last step (for the roofline):
+ * total milliseconds and launches of the histogram/split kernel, plus its
+ * algorithmic bytes (bin gathers + row-state reads) over those launches. */
+int boruta_session_kernel_stats(boruta_session* s, double* split_ms, int32_t* split_launches,
+                                double* split_bytes);
+
+void boruta_session_destroy(boruta_session* s);
+
+/* One node of a dumped tree. heap id: root 0, children 2v+1 (left) and 2v+2. */
+typedef struct {
+  uint64_t heap;
+  int32_t depth;
+  int32_t feature;  /* augmented column (originals first, then shadows); -1 = leaf */
+  int32_t bin;      /* rows with bin <= this go left */
+  uint32_t n_rows;  /* distinct in-bag rows at the node */
+  uint64_t n;       /* bootstrap-weighted rows */
+  int64_t stat[8];  /* weighted class counts, or stat[0] = sum of w*y (regression) */
+  double delta;     /* weighted impurity decrease of the split; 0 for leaves */
+} boruta_node;
+
+/* ---- device primitives, exposed for parity checks (device pointers) ----
+ * boruta_philox: out[4k..4k+3] = Philox4x32-10(ctr[4k..4k+3], key[0..1]) for k < n
+ *   (Salmon et al., SC'11), the generator behind every random draw.
+ * boruta_perm: out[k] = sigma(idx[k]) for the keyed Feistel permutation of
+ *   [0, n_domain) with counter words (w1, w2, w3) -- the Alg. 1 shuffle and
+ *   Alg. 3 flush_index construction.
+ * boruta_u256_to_double: out[k] = round-to-nearest-even of the 256-bit
+ *   integer v[4k..4k+3] (little-endian u64 limbs).
+ * boruta_binom_tails: for k < n, p_acc[k] = P(Bin(t[k], 1/2) >= h[k]) and
+ *   p_rej[k] = P(Bin(t[k], 1/2) <= h[k]), each rounded once (Alg. 1 test). */
+int boruta_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* stream);
+int boruta_perm(uint64_t n_domain, uint64_t seed, uint32_t w1, uint32_t w2, uint32_t w3,
+                const uint64_t* idx, uint64_t* out, int64_t count, void* stream);
+int boruta_u256_to_double(const uint64_t* v, double* out, int64_t n, void* stream);
+int boruta_binom_tails(const int32_t* t, const int32_t* h, double* p_acc, double* p_rej, int64_t n,
+                       void* stream);
+
+/* Message for the last error on this thread ("" if none). */
+const char* boruta_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,233 @@
+"""Thin Python binding of the C ABI in include/boruta.h (ctypes).
+
+Argument marshalling only: every step of the Boruta iteration runs in the
+CUDA kernels of libboruta_gb300.so.  PyTorch supplies device memory and the
+current stream.  There is no CPU fallback: if the library is missing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libboruta_gb300.so")
+_lib = None
+
+CLASSIFICATION, REGRESSION = 0, 1
+TREEIMP, PERMUT = 0, 2
+DUMP_SHADOW, DUMP_BOOT, DUMP_IMP, DUMP_STAT, DUMP_NODES, DUMP_TREE_PTR, DUMP_LIVE = range(1, 8)
+STATUS = {0: "BORUTA_OK", -1: "BORUTA_EINVAL", -2: "BORUTA_EOVERFLOW", -3: "BORUTA_ETIMEOUT",
+          -4: "BORUTA_ECUDA", -5: "BORUTA_ENOMEM"}
+
+# the exported symbols of include/boruta.h
+EXPORTS = [
+    "boruta_default_opts", "boruta_fit", "boruta_session_create", "boruta_session_step",
+    "boruta_session_read", "boruta_session_write", "boruta_session_dump",
+    "boruta_session_kernel_stats", "boruta_session_destroy", "boruta_philox", "boruta_perm",
+    "boruta_u256_to_double", "boruta_binom_tails", "boruta_last_error",
+]
+
+
+class BorutaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ct.Structure):
+    _fields_ = [("stat", ct.c_int), ("precision", ct.c_int), ("tie_break", ct.c_int),
+                ("n_classes", ct.c_int), ("kl_eps", ct.c_double), ("stream", ct.c_void_p),
+                ("job", ct.c_uint32), ("host_inputs", ct.c_int), ("graph", ct.c_int)]
+
+
+class Result(ct.Structure):
+    _fields_ = [("decision", ct.c_void_p), ("hits", ct.c_void_p), ("imp_history", ct.c_void_p),
+                ("shadow_max", ct.c_void_p), ("iterations", ct.c_int32)]
+
+
+NODE_DTYPE = np.dtype([
+    ("heap", "<u8"), ("depth", "<i4"), ("feature", "<i4"), ("bin", "<i4"), ("n_rows", "<u4"),
+    ("n", "<u8"), ("stat", "<i8", (8,)), ("delta", "<f8"),
+])
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Loads libboruta_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_2605_09950_gb300.build.build()")
+        L = ct.CDLL(_LIB_PATH)
+        vp, i64, i32 = ct.c_void_p, ct.c_int64, ct.c_int
+        fit_args = [vp, i64, vp, i64, i64, i32, i32, i32, i32, i32, i32, ct.c_double, ct.c_uint64,
+                    ct.POINTER(Opts)]
+        L.boruta_default_opts.argtypes = [ct.POINTER(Opts)]
+        L.boruta_default_opts.restype = None
+        L.boruta_fit.argtypes = fit_args + [ct.POINTER(Result)]
+        L.boruta_session_create.argtypes = fit_args + [ct.POINTER(vp)]
+        L.boruta_session_step.argtypes = [vp, ct.POINTER(ct.c_int32)]
+        L.boruta_session_read.argtypes = [vp, vp, vp, vp, vp, ct.POINTER(ct.c_int32)]
+        L.boruta_session_write.argtypes = [vp, vp, vp, vp, vp, ct.c_int32]
+        L.boruta_session_dump.argtypes = [vp, i32, vp, i64, ct.POINTER(i64)]
+        L.boruta_session_kernel_stats.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int32),
+                                                  ct.POINTER(ct.c_double)]
+        L.boruta_session_destroy.argtypes = [vp]
+        L.boruta_session_destroy.restype = None
+        L.boruta_philox.argtypes = [vp, vp, vp, i64, vp]
+        L.boruta_perm.argtypes = [ct.c_uint64, ct.c_uint64, ct.c_uint32, ct.c_uint32, ct.c_uint32, vp, vp,
+                                  i64, vp]
+        L.boruta_u256_to_double.argtypes = [vp, vp, i64, vp]
+        L.boruta_binom_tails.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.boruta_last_error.restype = ct.c_char_p
+        for name in EXPORTS:
+            if name not in ("boruta_default_opts", "boruta_session_destroy", "boruta_last_error"):
+                getattr(L, name).restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise BorutaError(rc, lib().boruta_last_error().decode())
+
+
+def _stream():
+    import torch
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def make_opts(stat=0, precision=0, tie_break=0, n_classes=0, kl_eps=1e-7, job=0, host_inputs=0,
+              graph=0, stream=None) -> Opts:
+    o = Opts()
+    lib().boruta_default_opts(ct.byref(o))
+    o.stat, o.precision, o.tie_break, o.n_classes = stat, precision, tie_break, n_classes
+    o.kl_eps, o.job, o.host_inputs, o.graph = kl_eps, job, host_inputs, graph
+    o.stream = stream if stream is not None else (None if host_inputs else _stream())
+    return o
+
+
+def _xy(X, y, N, host_inputs):
+    """(pointer, ld, N, p) for X given as a (p, ld) uint8 tensor / array."""
+    if host_inputs:
+        Xa = np.ascontiguousarray(X, dtype=np.uint8)
+        ya = np.ascontiguousarray(y)
+        return Xa.ctypes.data, Xa.shape[1], (Xa.shape[1] if N is None else N), Xa.shape[0], ya.ctypes.data, (Xa, ya)
+    import torch
+    assert X.is_cuda and X.dtype == torch.uint8 and X.is_contiguous() and X.dim() == 2
+    assert y.is_cuda and y.is_contiguous()
+    return X.data_ptr(), X.shape[1], (X.shape[1] if N is None else N), X.shape[0], y.data_ptr(), (X, y)
+
+
+def boruta_fit(X, y, task, n_trees, max_depth, mtry, n_bins, max_iter, alpha, seed, N=None, **opts):
+    """Alg. 1 on one problem.  X: (p, ld) uint8 (CUDA tensor, or numpy with
+    host_inputs=1), column j = X[j, :N]; y: uint8 labels or int64 fixed point."""
+    host = opts.get("host_inputs", 0)
+    xp, ld, N, p, yp, keep = _xy(X, y, N, host)
+    o = make_opts(**opts)
+    dec = np.zeros(p, np.int8)
+    hits = np.zeros(p, np.int32)
+    hist = np.zeros((max_iter, p))
+    smax = np.zeros(max_iter)
+    res = Result(dec.ctypes.data, hits.ctypes.data, hist.ctypes.data, smax.ctypes.data, 0)
+    _check(lib().boruta_fit(xp, ld, yp, N, p, task, n_trees, max_depth, mtry, n_bins, max_iter, alpha,
+                            seed, ct.byref(o), ct.byref(res)))
+    del keep
+    return dict(decision=dec, hits=hits, imp_history=hist, shadow_max=smax, iterations=res.iterations)
+
+
+class Session:
+    """Step-wise Boruta (boruta_session_*): one iteration per step()."""
+
+    def __init__(self, X, y, task, n_trees, max_depth, mtry, n_bins, max_iter, alpha, seed, N=None, **opts):
+        host = opts.get("host_inputs", 0)
+        xp, ld, N, p, yp, self._keep = _xy(X, y, N, host)
+        self.p, self.N, self.max_iter, self.n_trees = p, N, max_iter, n_trees
+        self._opts = make_opts(**opts)
+        h = ct.c_void_p()
+        _check(lib().boruta_session_create(xp, ld, yp, N, p, task, n_trees, max_depth, mtry, n_bins,
+                                           max_iter, alpha, seed, ct.byref(self._opts), ct.byref(h)))
+        self._h = h
+
+    def step(self) -> int:
+        und = ct.c_int32()
+        _check(lib().boruta_session_step(self._h, ct.byref(und)))
+        return und.value
+
+    def read(self):
+        dec = np.zeros(self.p, np.int8)
+        hits = np.zeros(self.p, np.int32)
+        hist = np.zeros((self.max_iter, self.p))
+        smax = np.zeros(self.max_iter)
+        t = ct.c_int32()
+        _check(lib().boruta_session_read(self._h, dec.ctypes.data, hits.ctypes.data, hist.ctypes.data,
+                                         smax.ctypes.data, ct.byref(t)))
+        return dict(decision=dec, hits=hits, imp_history=hist, shadow_max=smax, iterations=t.value)
+
+    def write(self, state):
+        dec = np.ascontiguousarray(state["decision"], np.int8)
+        hits = np.ascontiguousarray(state["hits"], np.int32)
+        hist = np.ascontiguousarray(state["imp_history"], np.float64)
+        smax = np.ascontiguousarray(state["shadow_max"], np.float64)
+        _check(lib().boruta_session_write(self._h, dec.ctypes.data, hits.ctypes.data, hist.ctypes.data,
+                                          smax.ctypes.data, int(state["iterations"])))
+
+    def dump(self, what, dtype):
+        need = ct.c_int64()
+        _check(lib().boruta_session_dump(self._h, what, None, 0, ct.byref(need)))
+        buf = np.zeros(need.value, dtype=np.uint8)
+        _check(lib().boruta_session_dump(self._h, what, buf.ctypes.data, buf.size, ct.byref(need)))
+        return buf.view(dtype)
+
+    def kernel_stats(self):
+        ms, n, b = ct.c_double(), ct.c_int32(), ct.c_double()
+        _check(lib().boruta_session_kernel_stats(self._h, ct.byref(ms), ct.byref(n), ct.byref(b)))
+        return dict(split_ms=ms.value, split_launches=n.value, split_bytes=b.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().boruta_session_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------- device primitives (torch CUDA tensors) ----------------
+
+def boruta_philox(ctr, key):
+    import torch
+    out = torch.empty_like(ctr)
+    _check(lib().boruta_philox(ctr.data_ptr(), key.data_ptr(), out.data_ptr(), ctr.numel() // 4, _stream()))
+    return out
+
+
+def boruta_perm(n, seed, w1, w2, w3, idx):
+    import torch
+    out = torch.empty_like(idx)
+    _check(lib().boruta_perm(n, seed, w1, w2, w3, idx.data_ptr(), out.data_ptr(), idx.numel(), _stream()))
+    return out
+
+
+def boruta_u256_to_double(v):
+    import torch
+    out = torch.empty(v.numel() // 4, dtype=torch.float64, device=v.device)
+    _check(lib().boruta_u256_to_double(v.data_ptr(), out.data_ptr(), out.numel(), _stream()))
+    return out
+
+
+def boruta_binom_tails(t, h):
+    import torch
+    pa = torch.empty(t.numel(), dtype=torch.float64, device=t.device)
+    pr = torch.empty_like(pa)
+    _check(lib().boruta_binom_tails(t.data_ptr(), h.data_ptr(), pa.data_ptr(), pr.data_ptr(), t.numel(),
+                                    _stream()))
+    return pa, pr

@@ -1,0 +1,631 @@
+// C ABI of the GPU Boruta library: argument checks, device workspace, the
+// per-iteration launch sequence (Alg. 1 loop body) and result transfer.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "boruta.h"
+#include "engine.cuh"
+
+using namespace bgb;
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(BORUTA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int64_t shadow_count(int64_t p_live) {
+  int64_t n = p_live;
+  if (n <= 0) return 0;
+  while (n < 5) n *= 2;
+  return n;
+}
+
+int64_t isqrt(int64_t v) {
+  int64_t r = static_cast<int64_t>(std::sqrt(static_cast<double>(v)));
+  while (r * r > v) --r;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return r;
+}
+
+}  // namespace
+
+struct boruta_session {
+  Dev d{};
+  cudaStream_t st = nullptr;
+  int64_t p = 0, N = 0;
+  int task = 0, mtry_opt = 0, max_iter = 0, t = 0;
+  bool finished = false;
+  std::vector<void*> dev_allocs;
+  std::vector<int8_t> state_h;
+  // pinned staging
+  uint32_t* status_h = nullptr;
+  int8_t* state_pin = nullptr;
+  int32_t* live_pin = nullptr;
+  const uint8_t** colptr_pin = nullptr;
+  // device per-iteration arrays
+  int32_t* live_d = nullptr;
+  const uint8_t** colptr_d = nullptr;
+  uint8_t* X_owned = nullptr;
+  void* y_owned = nullptr;
+  // launch geometry
+  int sms = 0, split_grid = 0, tree_grid = 0, permut_grid = 0;
+  size_t split_smem = 0;
+  // split-kernel timing of the last step
+  std::vector<cudaEvent_t> ev;
+  double split_ms = 0.0;
+  int split_launches = 0;
+  double split_bytes = 0.0;
+
+  template <typename T>
+  int alloc(T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BORUTA_ENOMEM, "device allocation of %zu bytes failed: %s", count * sizeof(T),
+                  cudaGetErrorString(e));
+    }
+    dev_allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return 0;
+  }
+
+  ~boruta_session() {
+    if (st) cudaStreamSynchronize(st);
+    for (void* q : dev_allocs) cudaFree(q);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (status_h) cudaFreeHost(status_h);
+    if (state_pin) cudaFreeHost(state_pin);
+    if (live_pin) cudaFreeHost(live_pin);
+    if (colptr_pin) cudaFreeHost(colptr_pin);
+  }
+};
+
+static int check_args(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p, int task,
+                      int n_trees, int max_depth, int mtry, int n_bins, int max_iter, double alpha,
+                      const boruta_opts* o) {
+  if (!X || !y) return fail(BORUTA_EINVAL, "X and y must not be NULL");
+  if (N < 1 || N >= (1 << 24)) return fail(BORUTA_EINVAL, "N = %lld outside [1, 2^24)", (long long)N);
+  if (p < 1 || p >= (1 << 23)) return fail(BORUTA_EINVAL, "p = %lld outside [1, 2^23)", (long long)p);
+  if (ld < N) return fail(BORUTA_EINVAL, "ld = %lld < N", (long long)ld);
+  if (task < 0 || task > 3) return fail(BORUTA_EINVAL, "task = %d is not kind | importance", task);
+  if (n_trees < 1 || n_trees >= (1 << 20)) return fail(BORUTA_EINVAL, "n_trees = %d", n_trees);
+  if (max_depth < 0 || max_depth > kMaxDepth) return fail(BORUTA_EINVAL, "max_depth = %d", max_depth);
+  if (n_bins < 2 || n_bins > 256) return fail(BORUTA_EINVAL, "n_bins = %d outside [2, 256]", n_bins);
+  if (max_iter < 1 || max_iter > 126) return fail(BORUTA_EINVAL, "max_iter = %d outside [1, 126]", max_iter);
+  if (!(alpha > 0.0)) return fail(BORUTA_EINVAL, "alpha must be positive");
+  if (mtry < 0) return fail(BORUTA_EINVAL, "mtry = %d", mtry);
+  if (o->n_classes < 0 || o->n_classes > kMaxClasses)
+    return fail(BORUTA_EINVAL, "n_classes = %d outside [0, 8]", o->n_classes);
+  if (o->precision < 0 || o->precision > 1 || o->tie_break < 0 || o->tie_break > 1 || o->stat < 0 ||
+      o->stat > 1)
+    return fail(BORUTA_EINVAL, "opts: precision, tie_break and stat take 0 or 1");
+  if (!(o->kl_eps > 0.0)) return fail(BORUTA_EINVAL, "kl_eps must be positive");
+  return 0;
+}
+
+extern "C" {
+
+void boruta_default_opts(boruta_opts* o) {
+  std::memset(o, 0, sizeof *o);
+  o->kl_eps = 1e-7;
+}
+
+const char* boruta_last_error(void) { return g_error.c_str(); }
+
+static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const void* y, int64_t N,
+                        int64_t p, int task, int n_trees, int max_depth, int mtry, int n_bins,
+                        int max_iter, double alpha, uint64_t seed, const boruta_opts* o) {
+  int rc;
+  s->st = static_cast<cudaStream_t>(o->stream);
+  s->p = p;
+  s->N = N;
+  s->task = task;
+  s->mtry_opt = mtry;
+  s->max_iter = max_iter;
+  Dev& d = s->d;
+  const bool reg = (task & 1) != 0;
+  d.kind = reg ? 1 : 0;
+  d.permut = (task & BORUTA_PERMUT) ? 1 : 0;
+  d.N = static_cast<int32_t>(N);
+  d.ldN = static_cast<int32_t>((N + 15) / 16 * 16);
+  d.p = static_cast<int32_t>(p);
+  d.B = n_bins;
+  d.D = max_depth;
+  d.M = n_trees;
+  d.max_iter = max_iter;
+  d.precision = o->precision;
+  d.tie_break = o->tie_break;
+  d.stat = o->stat;
+  d.seed = seed;
+  d.job = o->job;
+  d.kl_eps = o->kl_eps;
+  d.alpha = alpha;
+
+  const size_t ybytes = reg ? sizeof(int64_t) : sizeof(uint8_t);
+  if (o->host_inputs) {
+    if ((rc = s->alloc(&s->X_owned, static_cast<size_t>(ld) * p))) return rc;
+    CK(cudaMemcpyAsync(s->X_owned, X, static_cast<size_t>(ld) * p, cudaMemcpyHostToDevice, s->st));
+    uint8_t* yb = nullptr;
+    if ((rc = s->alloc(&yb, ybytes * N))) return rc;
+    CK(cudaMemcpyAsync(yb, y, ybytes * N, cudaMemcpyHostToDevice, s->st));
+    s->y_owned = yb;
+    d.X = s->X_owned;
+    y = yb;
+  } else {
+    d.X = X;
+  }
+  d.ld = ld;
+  d.ycls = reg ? nullptr : static_cast<const uint8_t*>(y);
+  d.yreg = reg ? static_cast<const int64_t*>(y) : nullptr;
+
+  const int64_t p_aug_max = p + shadow_count(p);
+  const int64_t n_sha_max = shadow_count(p);
+  // node pool: per tree at most min(2^l, N) nodes at depth l
+  uint64_t per_tree = 0;
+  for (int l = 0; l <= max_depth; ++l) per_tree += std::min<uint64_t>(1ull << l, static_cast<uint64_t>(N));
+  uint64_t cap = per_tree * static_cast<uint64_t>(n_trees);
+  if (cap > 0xFFFFFFF0ull) cap = 0xFFFFFFF0ull;
+  d.cap = static_cast<uint32_t>(cap);
+  const int Cmax = kMaxClasses;
+
+  if ((rc = s->alloc(&s->live_d, p))) return rc;
+  if ((rc = s->alloc(&s->colptr_d, p_aug_max))) return rc;
+  d.live = s->live_d;
+  d.colptr = s->colptr_d;
+  if ((rc = s->alloc(&d.Xsha, static_cast<size_t>(n_sha_max) * d.ldN))) return rc;
+  const size_t MN = static_cast<size_t>(n_trees) * N;
+  if ((rc = s->alloc(&d.bootcnt, MN))) return rc;
+  if ((rc = s->alloc(&d.rows[0], MN))) return rc;
+  if ((rc = s->alloc(&d.rows[1], MN))) return rc;
+  if ((rc = s->alloc(&d.oob, MN))) return rc;
+  if ((rc = s->alloc(&d.oob_cnt, n_trees))) return rc;
+  const size_t P = cap;
+  if ((rc = s->alloc(&d.nd_tree, P))) return rc;
+  if ((rc = s->alloc(&d.nd_heap, P))) return rc;
+  if ((rc = s->alloc(&d.nd_seg, P))) return rc;
+  if ((rc = s->alloc(&d.nd_len, P))) return rc;
+  if ((rc = s->alloc(&d.nd_n, P))) return rc;
+  if ((rc = s->alloc(&d.nd_split, P))) return rc;
+  if ((rc = s->alloc(&d.nd_child, P))) return rc;
+  if ((rc = s->alloc(&d.nd_delta, P))) return rc;
+  if ((rc = s->alloc(&d.nd_lrows, P))) return rc;
+  if ((rc = s->alloc(&d.nd_ln, P))) return rc;
+  if (reg) {
+    if ((rc = s->alloc(&d.nd_S, P))) return rc;
+    if ((rc = s->alloc(&d.nd_lS, P))) return rc;
+  }
+  if ((rc = s->alloc(&d.lvl_off, max_depth + 2))) return rc;
+  if ((rc = s->alloc(&d.lvl_cnt, max_depth + 2))) return rc;
+  if ((rc = s->alloc(&d.work, max_depth + 2))) return rc;
+  if ((rc = s->alloc(&d.chunk, kScanBlocks))) return rc;
+  if ((rc = s->alloc(&d.acc, static_cast<size_t>(n_trees) * p_aug_max * kFixLimbs))) return rc;
+  if ((rc = s->alloc(&d.imp, static_cast<size_t>(n_trees) * p_aug_max))) return rc;
+  if ((rc = s->alloc(&d.s, p_aug_max))) return rc;
+  if ((rc = s->alloc(&d.state, p))) return rc;
+  if ((rc = s->alloc(&d.hits, p))) return rc;
+  if ((rc = s->alloc(&d.hist, static_cast<size_t>(max_iter) * p))) return rc;
+  if ((rc = s->alloc(&d.smax, max_iter))) return rc;
+  if ((rc = s->alloc(&d.status, 4))) return rc;
+  if ((rc = s->alloc(&d.counters, 4))) return rc;
+  u128* pascal = nullptr;
+  if ((rc = s->alloc(&pascal, 127 * 127))) return rc;
+  d.pascal = pascal;
+
+  CK(cudaHostAlloc(&s->status_h, 4 * sizeof(uint32_t), cudaHostAllocDefault));
+  CK(cudaHostAlloc(&s->state_pin, p, cudaHostAllocDefault));
+  CK(cudaHostAlloc(&s->live_pin, p * sizeof(int32_t), cudaHostAllocDefault));
+  CK(cudaHostAlloc(reinterpret_cast<void**>(&s->colptr_pin), p_aug_max * sizeof(void*), cudaHostAllocDefault));
+
+  // binomial coefficients C(t, k), t, k <= 126, by Pascal's rule (exact)
+  std::vector<u128> tri(127 * 127, 0);
+  tri[0] = 1;
+  for (int t = 1; t <= 126; ++t) {
+    tri[t * 127] = 1;
+    for (int k = 1; k <= t; ++k) tri[t * 127 + k] = tri[(t - 1) * 127 + k - 1] + tri[(t - 1) * 127 + k];
+  }
+  CK(cudaMemcpyAsync(pascal, tri.data(), tri.size() * sizeof(u128), cudaMemcpyHostToDevice, s->st));
+
+  // state: all undecided, history NaN
+  CK(cudaMemsetAsync(d.state, 0, p, s->st));
+  CK(cudaMemsetAsync(d.hits, 0, p * sizeof(int32_t), s->st));
+  std::vector<double> nan_hist(static_cast<size_t>(max_iter) * p, std::nan(""));
+  CK(cudaMemcpyAsync(d.hist, nan_hist.data(), nan_hist.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(d.smax, nan_hist.data(), max_iter * sizeof(double), cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemsetAsync(d.status, 0, 4 * sizeof(uint32_t), s->st));
+  CK(cudaMemsetAsync(d.counters, 0, 4 * sizeof(unsigned long long), s->st));
+
+  // input validation on the device
+  d.C = 1;
+  launch_validate(d, s->st);
+  CK(cudaGetLastError());
+  unsigned long long maxy = 0;
+  CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(&maxy, d.counters + 1, sizeof maxy, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (s->status_h[0] & kErrInput)
+    return fail(BORUTA_EINVAL, "input has a bin >= n_bins (%d) or a label >= 8", n_bins);
+  if (reg) {
+    d.C = 1;
+    if (maxy && static_cast<double>(maxy) * static_cast<double>(N) >= 4611686018427387904.0)
+      return fail(BORUTA_EOVERFLOW, "N * max|y| must stay below 2^62");
+  } else {
+    const int seen = static_cast<int>(s->status_h[2]) + 1;
+    if (o->n_classes == 0) {
+      d.C = seen;
+    } else {
+      if (seen > o->n_classes) return fail(BORUTA_EINVAL, "label %d >= n_classes %d", seen - 1, o->n_classes);
+      d.C = o->n_classes;
+    }
+  }
+  if (!reg) {
+    if ((rc = s->alloc(&d.nd_cnt, P * d.C))) return rc;
+    if ((rc = s->alloc(&d.nd_lcnt, P * d.C))) return rc;
+  }
+  (void)Cmax;
+  CK(cudaMemsetAsync(d.status, 0, 4 * sizeof(uint32_t), s->st));
+
+  // launch geometry
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev));
+  s->split_smem = split_smem_bytes(d.kind, d.C, d.B);
+  CK(cudaFuncSetAttribute(split_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          static_cast<int>(s->split_smem)));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_kernel_ptr(), kSplitThreads, s->split_smem));
+  if (per_sm < 1) return fail(BORUTA_EINVAL, "split kernel does not fit on an SM");
+  s->split_grid = per_sm * s->sms;
+  s->tree_grid = std::min(n_trees, 8 * s->sms);
+  s->permut_grid = 16 * s->sms;
+  s->ev.resize(2 * (max_depth + 1));
+  for (auto& e : s->ev) CK(cudaEventCreate(&e));
+  s->state_h.assign(p, 0);
+  return 0;
+}
+
+int boruta_session_create(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p, int task,
+                          int n_trees, int max_depth, int mtry, int n_bins, int max_iter, double alpha,
+                          uint64_t seed, const boruta_opts* opts, boruta_session** out) {
+  if (!out) return fail(BORUTA_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  boruta_opts o;
+  if (opts)
+    o = *opts;
+  else
+    boruta_default_opts(&o);
+  int rc = check_args(X, ld, y, N, p, task, n_trees, max_depth, mtry, n_bins, max_iter, alpha, &o);
+  if (rc) return rc;
+  boruta_session* s = new boruta_session();
+  rc = session_init(s, X, ld, y, N, p, task, n_trees, max_depth, mtry, n_bins, max_iter, alpha, seed, &o);
+  if (rc) {
+    std::string msg = g_error;
+    delete s;
+    g_error = msg;
+    return rc;
+  }
+  *out = s;
+  return 0;
+}
+
+int boruta_session_step(boruta_session* s, int32_t* undecided) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  if (s->finished) return fail(BORUTA_EINVAL, "the run is finished (no undecided feature or t = max_iter)");
+  Dev& d = s->d;
+  cudaStream_t st = s->st;
+  const int t = s->t + 1;
+  // X_cur: undecided and accepted columns, in order
+  int32_t p_live = 0;
+  for (int64_t j = 0; j < s->p; ++j)
+    if (s->state_h[j] >= 0) s->live_pin[p_live++] = static_cast<int32_t>(j);
+  const int64_t n_sha = shadow_count(p_live);
+  const int64_t p_aug = p_live + n_sha;
+  for (int32_t a = 0; a < p_live; ++a) s->colptr_pin[a] = d.X + static_cast<int64_t>(s->live_pin[a]) * d.ld;
+  for (int64_t c = 0; c < n_sha; ++c) s->colptr_pin[p_live + c] = d.Xsha + c * d.ldN;
+  d.t = t;
+  d.p_live = p_live;
+  d.n_sha = static_cast<int32_t>(n_sha);
+  d.p_aug = static_cast<int32_t>(p_aug);
+  int64_t m = s->mtry_opt > 0 ? std::min<int64_t>(s->mtry_opt, p_aug)
+                              : (d.kind ? p_aug / 3 : isqrt(p_aug));
+  d.mtry = static_cast<int32_t>(std::max<int64_t>(m, 1));
+
+  CK(cudaMemcpyAsync(s->live_d, s->live_pin, p_live * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->colptr_d, s->colptr_pin, p_aug * sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d.bootcnt, 0, static_cast<size_t>(d.M) * d.N * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(d.acc, 0, static_cast<size_t>(d.M) * p_aug * kFixLimbs * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(d.work, 0, (d.D + 2) * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(d.lvl_cnt, 0, (d.D + 2) * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(d.counters, 0, sizeof(unsigned long long), st));
+
+  launch_shadow(d, st);
+  launch_bootstrap(d, s->tree_grid, st);
+  for (int level = 0; level < d.D; ++level) {
+    CK(cudaEventRecord(s->ev[2 * level], st));
+    launch_split(d, level, s->split_grid, s->split_smem, st);
+    CK(cudaEventRecord(s->ev[2 * level + 1], st));
+    launch_children(d, level, st);
+  }
+  if (d.permut)
+    launch_permut(d, s->permut_grid, st);
+  else
+    launch_treeimp(d, s->tree_grid, st);
+  launch_stats_decide(d, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(s->state_pin, d.state, s->p, cudaMemcpyDeviceToHost, st));
+  unsigned long long bytes = 0;
+  CK(cudaMemcpyAsync(&bytes, d.counters, sizeof bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint32_t err = s->status_h[0];
+  if (err) {
+    s->finished = true;
+    if (err & kErrPool) return fail(BORUTA_EOVERFLOW, "node pool capacity (%u) exceeded", d.cap);
+    if (err & kErrWeight) return fail(BORUTA_EOVERFLOW, "a bootstrap count exceeded 255");
+    if (err & kErrAcc) return fail(BORUTA_EOVERFLOW, "an importance term left the exact accumulator range");
+    if (err & kErrTimeout) return fail(BORUTA_ETIMEOUT, "a bounded device wait gave up");
+    return fail(BORUTA_EINVAL, "device reported error flags 0x%x", err);
+  }
+  s->split_ms = 0.0;
+  for (int level = 0; level < d.D; ++level) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, s->ev[2 * level], s->ev[2 * level + 1]));
+    s->split_ms += ms;
+  }
+  s->split_launches = d.D;
+  s->split_bytes = static_cast<double>(bytes);
+  std::memcpy(s->state_h.data(), s->state_pin, s->p);
+  s->t = t;
+  const int32_t und = static_cast<int32_t>(s->status_h[1]);
+  s->finished = und == 0 || t >= s->max_iter;
+  if (undecided) *undecided = und;
+  return 0;
+}
+
+int boruta_session_read(boruta_session* s, int8_t* decision, int32_t* hits, double* imp_history,
+                        double* shadow_max, int32_t* t) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  const Dev& d = s->d;
+  if (decision) CK(cudaMemcpyAsync(decision, d.state, s->p, cudaMemcpyDeviceToHost, s->st));
+  if (hits) CK(cudaMemcpyAsync(hits, d.hits, s->p * sizeof(int32_t), cudaMemcpyDeviceToHost, s->st));
+  if (imp_history)
+    CK(cudaMemcpyAsync(imp_history, d.hist, static_cast<size_t>(s->max_iter) * s->p * sizeof(double),
+                       cudaMemcpyDeviceToHost, s->st));
+  if (shadow_max)
+    CK(cudaMemcpyAsync(shadow_max, d.smax, s->max_iter * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (t) *t = s->t;
+  return 0;
+}
+
+int boruta_session_write(boruta_session* s, const int8_t* decision, const int32_t* hits,
+                         const double* imp_history, const double* shadow_max, int32_t t) {
+  if (!s || !decision || !hits || !imp_history || !shadow_max)
+    return fail(BORUTA_EINVAL, "session and all state buffers are required");
+  if (t < 0 || t > s->max_iter) return fail(BORUTA_EINVAL, "t = %d outside [0, max_iter]", t);
+  const Dev& d = s->d;
+  int64_t und = 0;
+  for (int64_t j = 0; j < s->p; ++j) {
+    if (decision[j] < -1 || decision[j] > 1) return fail(BORUTA_EINVAL, "decision values are -1, 0, 1");
+    und += decision[j] == 0;
+  }
+  CK(cudaMemcpyAsync(d.state, decision, s->p, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(d.hits, hits, s->p * sizeof(int32_t), cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(d.hist, imp_history, static_cast<size_t>(s->max_iter) * s->p * sizeof(double),
+                     cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(d.smax, shadow_max, s->max_iter * sizeof(double), cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  std::memcpy(s->state_h.data(), decision, s->p);
+  s->t = t;
+  s->finished = und == 0 || t >= s->max_iter;
+  return 0;
+}
+
+int boruta_session_kernel_stats(boruta_session* s, double* split_ms, int32_t* split_launches,
+                                double* split_bytes) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  if (split_ms) *split_ms = s->split_ms;
+  if (split_launches) *split_launches = s->split_launches;
+  if (split_bytes) *split_bytes = s->split_bytes;
+  return 0;
+}
+
+static int copy_out(boruta_session* s, const void* src, int64_t bytes, void* host, int64_t cap,
+                    int64_t* need) {
+  if (need) *need = bytes;
+  if (!host) return 0;
+  if (cap < bytes) return fail(BORUTA_EINVAL, "capacity %lld < %lld bytes", (long long)cap, (long long)bytes);
+  CK(cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return 0;
+}
+
+int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacity, int64_t* bytes) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  const Dev& d = s->d;
+  if (s->t == 0) return fail(BORUTA_EINVAL, "no iteration has run yet");
+  switch (what) {
+    case BORUTA_DUMP_SHADOW: {
+      const int64_t need = static_cast<int64_t>(d.n_sha) * d.N;
+      if (bytes) *bytes = need;
+      if (!host) return 0;
+      if (capacity < need) return fail(BORUTA_EINVAL, "capacity too small");
+      CK(cudaMemcpy2DAsync(host, d.N, d.Xsha, d.ldN, d.N, d.n_sha, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaStreamSynchronize(s->st));
+      return 0;
+    }
+    case BORUTA_DUMP_BOOT:
+      return copy_out(s, d.bootcnt, static_cast<int64_t>(d.M) * d.N * 4, host, capacity, bytes);
+    case BORUTA_DUMP_IMP:
+      return copy_out(s, d.imp, static_cast<int64_t>(d.M) * d.p_aug * 8, host, capacity, bytes);
+    case BORUTA_DUMP_STAT:
+      return copy_out(s, d.s, static_cast<int64_t>(d.p_aug) * 8, host, capacity, bytes);
+    case BORUTA_DUMP_LIVE:
+      return copy_out(s, s->live_d, static_cast<int64_t>(d.p_live) * 4, host, capacity, bytes);
+    case BORUTA_DUMP_NODES:
+    case BORUTA_DUMP_TREE_PTR: {
+      std::vector<uint32_t> off(d.D + 2), cnt(d.D + 2);
+      CK(cudaMemcpy(off.data(), d.lvl_off, (d.D + 2) * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(cnt.data(), d.lvl_cnt, (d.D + 2) * 4, cudaMemcpyDeviceToHost));
+      const uint32_t total = off[d.D] + cnt[d.D];
+      std::vector<uint32_t> tree(total), heap(total), len(total), n(total), split(total);
+      std::vector<double> delta(total);
+      std::vector<uint32_t> cnts(d.kind ? 0 : static_cast<size_t>(total) * d.C);
+      std::vector<int64_t> S(d.kind ? total : 0);
+      CK(cudaMemcpy(tree.data(), d.nd_tree, total * 4ull, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(heap.data(), d.nd_heap, total * 4ull, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(len.data(), d.nd_len, total * 4ull, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(n.data(), d.nd_n, total * 4ull, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(split.data(), d.nd_split, total * 4ull, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(delta.data(), d.nd_delta, total * 8ull, cudaMemcpyDeviceToHost));
+      if (d.kind)
+        CK(cudaMemcpy(S.data(), d.nd_S, total * 8ull, cudaMemcpyDeviceToHost));
+      else
+        CK(cudaMemcpy(cnts.data(), d.nd_cnt, cnts.size() * 4ull, cudaMemcpyDeviceToHost));
+      std::vector<std::vector<boruta_node>> per(d.M);
+      for (int l = 0; l <= d.D; ++l) {
+        for (uint32_t k = off[l]; k < off[l] + cnt[l]; ++k) {
+          boruta_node r;
+          std::memset(&r, 0, sizeof r);
+          r.heap = heap[k];
+          r.depth = l;
+          r.feature = split[k] == kLeaf ? -1 : static_cast<int32_t>(split[k] >> 8);
+          r.bin = split[k] == kLeaf ? 0 : static_cast<int32_t>(split[k] & 255u);
+          r.n_rows = len[k];
+          r.n = n[k];
+          if (d.kind)
+            r.stat[0] = S[k];
+          else
+            for (int c = 0; c < d.C; ++c) r.stat[c] = cnts[static_cast<size_t>(k) * d.C + c];
+          r.delta = split[k] == kLeaf ? 0.0 : delta[k];
+          per[tree[k]].push_back(r);
+        }
+      }
+      if (what == BORUTA_DUMP_TREE_PTR) {
+        const int64_t need = static_cast<int64_t>(d.M + 1) * 8;
+        if (bytes) *bytes = need;
+        if (!host) return 0;
+        if (capacity < need) return fail(BORUTA_EINVAL, "capacity too small");
+        int64_t* o = static_cast<int64_t*>(host);
+        o[0] = 0;
+        for (int tau = 0; tau < d.M; ++tau) o[tau + 1] = o[tau] + static_cast<int64_t>(per[tau].size());
+        return 0;
+      }
+      const int64_t need = static_cast<int64_t>(total) * sizeof(boruta_node);
+      if (bytes) *bytes = need;
+      if (!host) return 0;
+      if (capacity < need) return fail(BORUTA_EINVAL, "capacity too small");
+      boruta_node* o = static_cast<boruta_node*>(host);
+      for (int tau = 0; tau < d.M; ++tau)
+        for (const auto& r : per[tau]) *o++ = r;
+      return 0;
+    }
+    default:
+      return fail(BORUTA_EINVAL, "unknown dump %d", what);
+  }
+}
+
+void boruta_session_destroy(boruta_session* s) { delete s; }
+
+int boruta_fit(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p, int task, int n_trees,
+               int max_depth, int mtry, int n_bins, int max_iter, double alpha, uint64_t seed,
+               const boruta_opts* opts, boruta_result* out) {
+  if (!out || !out->decision || !out->hits || !out->imp_history || !out->shadow_max)
+    return fail(BORUTA_EINVAL, "out and its buffers must not be NULL");
+  boruta_session* s = nullptr;
+  int rc = boruta_session_create(X, ld, y, N, p, task, n_trees, max_depth, mtry, n_bins, max_iter,
+                                 alpha, seed, opts, &s);
+  if (rc) return rc;
+  int32_t und = 1;
+  while (!s->finished) {
+    rc = boruta_session_step(s, &und);
+    if (rc) break;
+  }
+  int32_t t = 0;
+  if (!rc) rc = boruta_session_read(s, out->decision, out->hits, out->imp_history, out->shadow_max, &t);
+  out->iterations = t;
+  std::string msg = g_error;
+  boruta_session_destroy(s);
+  g_error = msg;
+  return rc;
+}
+
+// ---------------------------------------------------------------- primitives
+int boruta_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(BORUTA_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n) launch_debug_philox(ctr, key, out, n, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int boruta_perm(uint64_t n_domain, uint64_t seed, uint32_t w1, uint32_t w2, uint32_t w3,
+                const uint64_t* idx, uint64_t* out, int64_t count, void* stream) {
+  if (n_domain < 1 || n_domain > 0xFFFFFFFFull || count < 0) return fail(BORUTA_EINVAL, "bad domain");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (count) launch_debug_perm(static_cast<uint32_t>(n_domain), seed, w1, w2, w3, idx, out, count, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int boruta_u256_to_double(const uint64_t* v, double* out, int64_t n, void* stream) {
+  if (n < 0) return fail(BORUTA_EINVAL, "bad size");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n) launch_debug_u256(v, out, n, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int boruta_binom_tails(const int32_t* t, const int32_t* h, double* p_acc, double* p_rej, int64_t n,
+                       void* stream) {
+  if (n < 0) return fail(BORUTA_EINVAL, "bad size");
+  if (n == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<int32_t> th(n);
+  CK(cudaMemcpyAsync(th.data(), t, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < n; ++i)
+    if (th[i] < 0 || th[i] > 126) return fail(BORUTA_EINVAL, "t[%lld] = %d outside [0, 126]", (long long)i, th[i]);
+  std::vector<u128> tri(127 * 127, 0);
+  tri[0] = 1;
+  for (int r = 1; r <= 126; ++r) {
+    tri[r * 127] = 1;
+    for (int k = 1; k <= r; ++k) tri[r * 127 + k] = tri[(r - 1) * 127 + k - 1] + tri[(r - 1) * 127 + k];
+  }
+  void* dt = nullptr;
+  CK(cudaMalloc(&dt, tri.size() * sizeof(u128)));
+  cudaError_t e = cudaMemcpy(dt, tri.data(), tri.size() * sizeof(u128), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    launch_debug_binom(static_cast<const u128*>(dt), t, h, p_acc, p_rej, n, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(dt);
+  if (e != cudaSuccess) return fail(BORUTA_ECUDA, "binom tails: %s", cudaGetErrorString(e));
+  return 0;
+}
+
+}  // extern "C"

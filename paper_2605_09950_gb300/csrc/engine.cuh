@@ -1,0 +1,90 @@
+// Internal interface between the host driver (api.cu) and the kernels (kernels.cu).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace bgb {
+
+// Everything a kernel needs, passed by value.  Sizes are fixed for a
+// session except the per-iteration block (t, p_live, n_sha, p_aug, mtry).
+struct Dev {
+  // ---- problem
+  const uint8_t* X;        // column-major bins, column j at X + j*ld
+  int64_t ld;
+  const uint8_t* ycls;     // labels (classification)
+  const int64_t* yreg;     // fixed-point targets (regression)
+  int32_t N, ldN, p, kind, C, B, D, M, max_iter;
+  int32_t precision, tie_break, stat, permut;
+  uint64_t seed;
+  uint32_t job;
+  double kl_eps, alpha;
+  // ---- iteration
+  int32_t t, p_live, n_sha, p_aug, mtry;
+  const int32_t* live;           // [p_live]
+  const uint8_t* const* colptr;  // [p_aug] augmented column pointers
+  // ---- buffers
+  uint8_t* Xsha;                 // [n_sha][ldN]
+  uint32_t* bootcnt;             // [M][N] bootstrap draw counts
+  uint32_t* rows[2];             // [M][N] node-ordered row entries (row << 8 | weight)
+  uint32_t* oob;                 // [M][N] out-of-bag rows, ascending
+  uint32_t* oob_cnt;             // [M]
+  // ---- node pool (level-major; within a level, ordered by (tree, heap))
+  uint32_t cap;
+  uint32_t *nd_tree, *nd_heap, *nd_seg, *nd_len, *nd_n;
+  uint32_t* nd_cnt;              // [cap][C] weighted class counts
+  int64_t* nd_S;                 // [cap] weighted target sum
+  uint32_t *nd_split, *nd_child; // split = feature << 8 | bin, kLeaf for leaves
+  double* nd_delta;
+  uint32_t *nd_lrows, *nd_ln;    // left child: distinct rows, weighted rows
+  uint32_t* nd_lcnt;             // [cap][C]
+  int64_t* nd_lS;
+  uint32_t *lvl_off, *lvl_cnt;   // [D + 2]
+  uint32_t* work;                // [D + 2] node claim counters
+  uint32_t* chunk;               // [kScanBlocks] per-block split counts
+  // ---- importance and Boruta state
+  unsigned long long* acc;       // [M][p_aug][6] exact per-tree accumulators
+  double* imp;                   // [M][p_aug]
+  double* s;                     // [p_aug]
+  const u128* pascal;            // [127][127] binomial coefficients C(t, k)
+  int8_t* state;                 // [p]
+  int32_t* hits;                 // [p]
+  double* hist;                  // [max_iter][p]
+  double* smax;                  // [max_iter]
+  uint32_t* status;              // [0] error flags, [1] undecided count, [2] n_classes seen
+  unsigned long long* counters;  // [0] split-kernel algorithmic bytes, [1] max |y|
+};
+
+constexpr int kScanBlocks = 512;
+constexpr int kSplitThreads = 256;
+
+// launchers (kernels.cu)
+void launch_validate(const Dev& d, cudaStream_t st);
+void launch_shadow(const Dev& d, cudaStream_t st);
+void launch_bootstrap(const Dev& d, int grid, cudaStream_t st);
+void launch_split(const Dev& d, int level, int grid, size_t smem, cudaStream_t st);
+void launch_children(const Dev& d, int level, cudaStream_t st);
+void launch_treeimp(const Dev& d, int grid, cudaStream_t st);
+void launch_permut(const Dev& d, int grid, cudaStream_t st);
+void launch_stats_decide(const Dev& d, cudaStream_t st);
+// dynamic shared memory of k_split: one histogram per warp, 16-byte aligned
+__host__ __device__ inline size_t split_smem_per_warp(int kind, int C, int B) {
+  const size_t b = kind == 0 ? static_cast<size_t>(B) * C * 4 : static_cast<size_t>(B + 2) * 12;
+  return (b + 15) & ~static_cast<size_t>(15);
+}
+__host__ __device__ inline size_t split_smem_bytes(int kind, int C, int B) {
+  return (kSplitThreads / 32) * split_smem_per_warp(kind, C, B);
+}
+const void* split_kernel_ptr();
+
+void launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                         cudaStream_t st);
+void launch_debug_perm(uint32_t n, uint64_t seed, uint32_t w1, uint32_t w2, uint32_t w3,
+                       const uint64_t* idx, uint64_t* out, int64_t count, cudaStream_t st);
+void launch_debug_u256(const uint64_t* v, double* out, int64_t n, cudaStream_t st);
+void launch_debug_binom(const u128* pascal, const int32_t* t, const int32_t* h, double* pa,
+                        double* pr, int64_t n, cudaStream_t st);
+
+}  // namespace bgb

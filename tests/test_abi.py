@@ -1,0 +1,71 @@
+"""The C ABI without a GPU: the library builds, loads, exports every entry
+point include/boruta.h declares, and rejects bad arguments on the host."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_09950_gb300 import boruta, build
+
+    build.build()
+    return boruta.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "boruta.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(boruta_\w+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    from paper_2605_09950_gb300 import boruta
+
+    assert declared_functions() == sorted(boruta.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_default_opts(lib):
+    from paper_2605_09950_gb300 import boruta
+
+    o = boruta.Opts()
+    lib.boruta_default_opts(o)
+    assert o.kl_eps == 1e-7 and o.precision == 0 and o.tie_break == 0 and o.stat == 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(N=0), dict(N=1 << 24), dict(n_bins=1), dict(n_bins=257), dict(max_iter=0), dict(max_iter=127),
+    dict(max_depth=31), dict(n_trees=0), dict(alpha=0.0), dict(task=4), dict(mtry=-1),
+    dict(n_classes=9), dict(precision=2),
+])
+def test_invalid_arguments_are_rejected_on_the_host(lib, bad):
+    from paper_2605_09950_gb300 import boruta
+
+    X = np.zeros((3, 16), np.uint8)
+    y = np.zeros(16, np.uint8)
+    args = dict(task=0, n_trees=2, max_depth=3, mtry=0, n_bins=4, max_iter=3, alpha=0.01, seed=0, N=16)
+    opts = dict(host_inputs=1)
+    for k, v in bad.items():
+        (opts if k in ("n_classes", "precision") else args)[k] = v
+    with pytest.raises(boruta.BorutaError) as e:
+        boruta.boruta_fit(X, y, **args, **opts)
+    assert e.value.code == -1
+    assert str(e.value)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2605_09950_gb300 import boruta
+
+    monkeypatch.setattr(boruta, "_lib", None)
+    monkeypatch.setattr(boruta, "_LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        boruta.lib()

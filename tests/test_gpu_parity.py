@@ -1,0 +1,277 @@
+"""CUDA path against the CPU oracle, element by element on the same seeded
+inputs (through the C ABI).
+
+Bar: trees, bootstrap counts, shadow columns, hits and decisions bit-exact;
+FP64 TreeImp and regression Permut importances bit-exact (both sides sum
+exactly and round once); classification Permut importances within 1e-12
+relative (the KL loss calls log, whose last bit may differ between CUDA and
+the C library); the FP32 form within 1e-5 relative of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_09950_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-12
+REL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def session(w, **opts):
+    import torch
+
+    from paper_2605_09950_gb300 import boruta
+
+    X = torch.from_numpy(w.X).cuda()
+    y = torch.from_numpy(w.y).cuda()
+    params = w.params()
+    n_classes = params.pop("n_classes")
+    return boruta.Session(X, y, N=w.N, n_classes=n_classes, **params, **opts)
+
+
+def oracle_problem(w, **kw):
+    return oracle.BorutaProblem(w.X, w.y, **w.params(), N=w.N, **kw)
+
+
+def close(a, b, rel):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    assert a.shape == b.shape
+    both_nan = np.isnan(a) & np.isnan(b)
+    ok = both_nan | (a == b) | (np.abs(a - b) <= rel * np.maximum(np.abs(a), np.abs(b)))
+    assert ok.all(), (a[~ok][:5], b[~ok][:5])
+
+
+def compare_nodes(g, o, exact_delta=True, rel=REL32):
+    assert len(g) == len(o), (len(g), len(o))
+    for k in ("heap", "depth", "feature", "bin", "n_rows", "n"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    np.testing.assert_array_equal(g["stat"], o["stat"])
+    if exact_delta:
+        np.testing.assert_array_equal(g["delta"], o["delta"])
+    else:
+        close(g["delta"], o["delta"], rel)
+
+
+def check_iteration(w, trees=None, precision=0, state=None, t=1, tie_break=0):
+    """Runs iteration t on the GPU and checks every dump against the oracle."""
+    from paper_2605_09950_gb300 import boruta
+
+    S = session(w, precision=precision, tie_break=tie_break)
+    p = w.p
+    if state is None:
+        state = dict(decision=np.zeros(p, np.int8), hits=np.zeros(p, np.int32),
+                     imp_history=np.full((w.max_iter, p), np.nan), shadow_max=np.full(w.max_iter, np.nan),
+                     iterations=t - 1)
+    S.write(state)
+    S.step()
+    P = oracle_problem(w, tie_break=tie_break)
+    live = P.live(state["decision"])
+    np.testing.assert_array_equal(S.dump(boruta.DUMP_LIVE, np.int32), live)
+    sha_o = P.shadow(t, live)
+    sha_g = S.dump(boruta.DUMP_SHADOW, np.uint8).reshape(sha_o.shape)
+    np.testing.assert_array_equal(sha_g, sha_o)
+    boot = S.dump(boruta.DUMP_BOOT, np.uint32).reshape(w.n_trees, w.N)
+    nodes = S.dump(boruta.DUMP_NODES, boruta.NODE_DTYPE)
+    ptr = S.dump(boruta.DUMP_TREE_PTR, np.int64)
+    imp = S.dump(boruta.DUMP_IMP, np.float64).reshape(w.n_trees, -1)
+    permut = (w.task & 2) != 0
+    reg = (w.task & 1) == 1
+    for tau in (trees if trees is not None else range(w.n_trees)):
+        np.testing.assert_array_equal(boot[tau], oracle.bootstrap(w.seed, 0, t, tau, w.N))
+        nd, ti, pm = P.tree(t, live, sha_o, tau, treeimp=not permut, permut=permut)
+        compare_nodes(nodes[ptr[tau]:ptr[tau + 1]], nd, exact_delta=precision == 0)
+        want = pm if permut else ti
+        if precision == 1:
+            close(imp[tau], want, REL32)
+        elif permut and not reg:
+            close(imp[tau], want, REL64)
+        else:
+            np.testing.assert_array_equal(imp[tau], want)
+    return S, P, state, imp
+
+
+# ---------------------------------------------------------------- single iterations
+
+@pytest.mark.parametrize("importance", [0, 2])
+def test_binary_iteration(importance):
+    w = synth.binary_small(N=500, p=20, n_inf=4, n_trees=16, max_depth=7, max_iter=5, importance=importance)
+    S, P, st, imp = check_iteration(w)
+    o = P.iteration(1, st["decision"], st["hits"])
+    from paper_2605_09950_gb300 import boruta
+
+    s = S.dump(boruta.DUMP_STAT, np.float64)
+    if importance == 0:
+        np.testing.assert_array_equal(s, o["s"])
+    else:
+        close(s, o["s"], 1e-9)
+    g = S.read()
+    np.testing.assert_array_equal(g["hits"], o["hits"])
+    np.testing.assert_array_equal(g["decision"], o["state"])
+
+
+@pytest.mark.parametrize("importance", [0, 2])
+def test_multiclass_iteration(importance):
+    w = synth.multiclass_toeplitz(N=3000, p=30, block=10, n_inf=3, n_classes=5, n_trees=10, max_depth=9,
+                                  max_iter=3, importance=importance)
+    check_iteration(w)
+
+
+@pytest.mark.parametrize("importance", [0, 2])
+def test_regression_iteration(importance):
+    w = synth.snp_regression(N=900, p=40, n_add=5, n_pairs=2, n_trees=10, max_depth=7, max_iter=3,
+                             importance=importance)
+    check_iteration(w)
+
+
+@pytest.mark.parametrize("importance", [0, 2])
+def test_fp32_form_iteration(importance):
+    w = synth.binary_small(N=700, p=25, n_inf=5, n_trees=12, max_depth=8, max_iter=3, importance=importance)
+    check_iteration(w, precision=1)
+    w = synth.snp_regression(N=600, p=30, n_add=4, n_pairs=2, n_trees=6, max_depth=6, max_iter=3,
+                             importance=importance)
+    check_iteration(w, precision=1)
+
+
+def test_lowest_index_tie_break():
+    w = synth.binary_small(N=300, p=10, n_inf=2, n_trees=8, max_depth=8, max_iter=3)
+    check_iteration(w, tie_break=1)
+
+
+def test_later_iteration_with_rejected_columns():
+    """t = 9 with some columns rejected and some accepted: the live list,
+    shadow doubling (p_live < 5) and hit bookkeeping follow the state."""
+    w = synth.binary_small(N=400, p=7, n_inf=2, n_trees=8, max_depth=6, max_iter=12)
+    dec = np.array([1, -1, 0, -1, -1, 0, -1], np.int8)
+    hits = np.array([8, 0, 4, 1, 0, 2, 0], np.int32)
+    hist = np.full((12, 7), np.nan)
+    smax = np.full(12, np.nan)
+    st = dict(decision=dec, hits=hits, imp_history=hist, shadow_max=smax, iterations=8)
+    S, P, _, _ = check_iteration(w, state=st, t=9)
+    o = P.iteration(9, dec, hits)
+    g = S.read()
+    np.testing.assert_array_equal(g["hits"], o["hits"])
+    np.testing.assert_array_equal(g["decision"], o["state"])
+    np.testing.assert_array_equal(g["imp_history"][8], o["hist"])
+    assert g["shadow_max"][8] == o["shadow_max"]
+
+
+# ---------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("case", ["ragged", "tiny", "one_row", "depth0", "two_bins", "full_mtry",
+                                  "constant", "deep_small"])
+def test_edge_cases(case):
+    if case == "ragged":      # N not a multiple of 16, dense and sparse node paths
+        w = synth.binary_small(N=37, p=3, n_inf=1, n_trees=6, max_depth=5, max_iter=2, n_bins=5)
+    elif case == "tiny":      # every node on the one-row-per-lane path
+        w = synth.binary_small(N=20, p=4, n_inf=1, n_trees=5, max_depth=10, max_iter=2, n_bins=8)
+    elif case == "one_row":
+        w = synth.binary_small(N=1, p=2, n_inf=1, n_trees=3, max_depth=4, max_iter=2, n_bins=4)
+        w.y[:] = 0
+    elif case == "depth0":    # stumps that never split: all importances 0
+        w = synth.binary_small(N=200, p=6, n_inf=2, n_trees=4, max_depth=0, max_iter=2)
+    elif case == "two_bins":
+        w = synth.binary_small(N=300, p=6, n_inf=2, n_trees=5, max_depth=6, max_iter=2, n_bins=2)
+    elif case == "full_mtry":
+        w = synth.binary_small(N=300, p=6, n_inf=2, n_trees=5, max_depth=6, max_iter=2)
+        w.mtry = 1000         # clamps to p_aug
+    elif case == "constant":
+        w = synth.binary_small(N=300, p=6, n_inf=2, n_trees=5, max_depth=6, max_iter=2, importance=2)
+        w.X[3, :] = 2
+    else:
+        w = synth.multiclass_toeplitz(N=2000, p=10, block=5, n_inf=2, n_classes=3, n_trees=4, max_depth=14,
+                                      max_iter=2, n_bins=256, importance=2)
+    check_iteration(w)
+
+
+# ---------------------------------------------------------------- whole runs
+
+@pytest.mark.parametrize("importance", [0, 2])
+def test_full_run_small(importance):
+    w = synth.binary_small(N=400, p=12, n_inf=3, n_trees=20, max_depth=6, max_iter=16, importance=importance)
+    from paper_2605_09950_gb300 import boruta
+    import torch
+
+    params = w.params()
+    nc = params.pop("n_classes")
+    g = boruta.boruta_fit(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.y).cuda(), N=w.N, n_classes=nc,
+                          **params)
+    o = oracle_problem(w).run()
+    assert g["iterations"] == o["iterations"]
+    np.testing.assert_array_equal(g["decision"], o["decision"])
+    np.testing.assert_array_equal(g["hits"], o["hits"])
+    if importance == 0:
+        np.testing.assert_array_equal(g["imp_history"], o["imp_history"])
+        np.testing.assert_array_equal(g["shadow_max"], o["shadow_max"])
+    else:
+        close(g["imp_history"], o["imp_history"], 1e-9)
+        close(g["shadow_max"], o["shadow_max"], 1e-9)
+
+
+def test_binary_n1000_p50_full_run():
+    """The small workload: binary N=1000, p=50, 100 trees, depth 8, TreeImp,
+    20 iterations -- bit-exact against the oracle, planted set recovered."""
+    import torch
+
+    from paper_2605_09950_gb300 import boruta
+
+    w = synth.binary_small()
+    params = w.params()
+    nc = params.pop("n_classes")
+    g = boruta.boruta_fit(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.y).cuda(), N=w.N, n_classes=nc,
+                          **params)
+    o = oracle_problem(w).run()
+    assert g["iterations"] == o["iterations"]
+    np.testing.assert_array_equal(g["decision"], o["decision"])
+    np.testing.assert_array_equal(g["hits"], o["hits"])
+    np.testing.assert_array_equal(g["imp_history"], o["imp_history"])
+    assert set(np.flatnonzero(g["decision"] == 1)) == set(w.informative.tolist())
+
+
+def test_checkpoint_resume_is_exact():
+    """Counter-based randomness: resuming from a state read at t = 4
+    reproduces the uninterrupted run bit for bit."""
+    w = synth.binary_small(N=400, p=12, n_inf=3, n_trees=12, max_depth=6, max_iter=14)
+    A = session(w)
+    while True:
+        if A.step() == 0 or A.read()["iterations"] == w.max_iter:
+            break
+    full = A.read()
+    B = session(w)
+    for _ in range(4):
+        B.step()
+    ck = B.read()
+    B.close()
+    C = session(w)
+    C.write(ck)
+    while C.read()["iterations"] < full["iterations"]:
+        C.step()
+    res = C.read()
+    for k in ("decision", "hits", "imp_history", "shadow_max"):
+        np.testing.assert_array_equal(res[k], full[k])
+
+
+# ---------------------------------------------------------------- full size, sampled
+
+def test_binary_n100000_p1000_sampled():
+    """Binary N=1e5, p=1000, 500 trees, depth 16 (one iteration, in the
+    launch configuration the benchmark times): trees 0 and 499 node by node
+    and their Permut rows against the oracle; properties of every tree."""
+    from paper_2605_09950_gb300 import boruta
+
+    w = synth.binary_wide(max_iter=3)
+    S, P, st, imp = check_iteration(w, trees=[0, 499])
+    boot = S.dump(boruta.DUMP_BOOT, np.uint32).reshape(w.n_trees, w.N)
+    assert (boot.sum(axis=1) == w.N).all()
+    assert np.isfinite(imp).all() and (imp >= -1e-15).all()

@@ -138,6 +138,8 @@ int boruta_session_write(boruta_session* s, const int8_t* decision, const int32_
  *   BORUTA_DUMP_NODES    boruta_node [count]  trees in order, each in (depth, heap) order
  *   BORUTA_DUMP_TREE_PTR int64  [M + 1]       offsets of each tree in the node dump
  *   BORUTA_DUMP_LIVE     int32  [p_live]      original columns in play
+ *   BORUTA_DUMP_LEVELS   double [max_depth+1][2]  nodes at each depth, milliseconds
+ *                        of the split kernel at that depth (0 for the last)
  * host must hold capacity bytes; *bytes receives the size needed (pass
  * host = NULL to query).  */
 #define BORUTA_DUMP_SHADOW 1
@@ -147,6 +149,7 @@ int boruta_session_write(boruta_session* s, const int8_t* decision, const int32_
 #define BORUTA_DUMP_NODES 5
 #define BORUTA_DUMP_TREE_PTR 6
 #define BORUTA_DUMP_LIVE 7
+#define BORUTA_DUMP_LEVELS 8
 int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacity, int64_t* bytes);
 
 /* Timing of the dominant kernel of the last step (for the roofline):

@@ -17,7 +17,7 @@ _lib = None
 
 CLASSIFICATION, REGRESSION = 0, 1
 TREEIMP, PERMUT = 0, 2
-DUMP_SHADOW, DUMP_BOOT, DUMP_IMP, DUMP_STAT, DUMP_NODES, DUMP_TREE_PTR, DUMP_LIVE = range(1, 8)
+DUMP_SHADOW, DUMP_BOOT, DUMP_IMP, DUMP_STAT, DUMP_NODES, DUMP_TREE_PTR, DUMP_LIVE, DUMP_LEVELS = range(1, 9)
 STATUS = {0: "BORUTA_OK", -1: "BORUTA_EINVAL", -2: "BORUTA_EOVERFLOW", -3: "BORUTA_ETIMEOUT",
           -4: "BORUTA_ECUDA", -5: "BORUTA_ENOMEM"}
 

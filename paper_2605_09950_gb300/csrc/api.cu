@@ -67,11 +67,12 @@ struct boruta_session {
   uint8_t* X_owned = nullptr;
   void* y_owned = nullptr;
   // launch geometry
-  int sms = 0, split_grid = 0, tree_grid = 0, permut_grid = 0;
+  int sms = 0, split_grid = 0, small_grid = 0, tree_grid = 0, permut_grid = 0;
   size_t split_smem = 0;
   // split-kernel timing of the last step
   std::vector<cudaEvent_t> ev;
   double split_ms = 0.0;
+  std::vector<double> level_ms;
   int split_launches = 0;
   double split_bytes = 0.0;
 
@@ -282,6 +283,12 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
     if ((rc = s->alloc(&d.nd_cnt, P * d.C))) return rc;
     if ((rc = s->alloc(&d.nd_lcnt, P * d.C))) return rc;
   }
+  // larger nodes of one level: at most N/33 per tree (each has > 32 rows)
+  const size_t big_cap = static_cast<size_t>(n_trees) * (static_cast<size_t>(N) / 33 + 1);
+  if ((rc = s->alloc(&d.big, big_cap))) return rc;
+  uint8_t* cand = nullptr;
+  if ((rc = s->alloc(&cand, big_cap * kItemsPerNode * cand_bytes(split_variant(d.kind, d.C))))) return rc;
+  d.cand = cand;
   (void)Cmax;
   CK(cudaMemsetAsync(d.status, 0, 4 * sizeof(uint32_t), s->st));
 
@@ -290,12 +297,13 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev));
   s->split_smem = split_smem_bytes(d.kind, d.C, d.B);
-  CK(cudaFuncSetAttribute(split_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          static_cast<int>(s->split_smem)));
+  const void* big = split_big_ptr(split_variant(d.kind, d.C));
+  CK(cudaFuncSetAttribute(big, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(s->split_smem)));
   int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_kernel_ptr(), kSplitThreads, s->split_smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big, kSplitThreads, s->split_smem));
   if (per_sm < 1) return fail(BORUTA_EINVAL, "split kernel does not fit on an SM");
   s->split_grid = per_sm * s->sms;
+  s->small_grid = 8 * s->sms;
   s->tree_grid = std::min(n_trees, 8 * s->sms);
   s->permut_grid = 16 * s->sms;
   s->ev.resize(2 * (max_depth + 1));
@@ -362,7 +370,7 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   launch_bootstrap(d, s->tree_grid, st);
   for (int level = 0; level < d.D; ++level) {
     CK(cudaEventRecord(s->ev[2 * level], st));
-    launch_split(d, level, s->split_grid, s->split_smem, st);
+    launch_split(d, level, s->small_grid, s->split_grid, s->split_smem, st);
     CK(cudaEventRecord(s->ev[2 * level + 1], st));
     launch_children(d, level, st);
   }
@@ -387,10 +395,12 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
     return fail(BORUTA_EINVAL, "device reported error flags 0x%x", err);
   }
   s->split_ms = 0.0;
+  s->level_ms.assign(d.D + 1, 0.0);
   for (int level = 0; level < d.D; ++level) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, s->ev[2 * level], s->ev[2 * level + 1]));
     s->split_ms += ms;
+    s->level_ms[level] = ms;
   }
   s->split_launches = d.D;
   s->split_bytes = static_cast<double>(bytes);
@@ -482,6 +492,20 @@ int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacit
       return copy_out(s, d.s, static_cast<int64_t>(d.p_aug) * 8, host, capacity, bytes);
     case BORUTA_DUMP_LIVE:
       return copy_out(s, s->live_d, static_cast<int64_t>(d.p_live) * 4, host, capacity, bytes);
+    case BORUTA_DUMP_LEVELS: {
+      const int64_t need = static_cast<int64_t>(d.D + 1) * 2 * 8;
+      if (bytes) *bytes = need;
+      if (!host) return 0;
+      if (capacity < need) return fail(BORUTA_EINVAL, "capacity too small");
+      std::vector<uint32_t> cnt(d.D + 2);
+      CK(cudaMemcpy(cnt.data(), d.lvl_cnt, (d.D + 2) * 4, cudaMemcpyDeviceToHost));
+      double* o = static_cast<double*>(host);
+      for (int l = 0; l <= d.D; ++l) {
+        o[2 * l] = cnt[l];
+        o[2 * l + 1] = l < static_cast<int>(s->level_ms.size()) ? s->level_ms[l] : 0.0;
+      }
+      return 0;
+    }
     case BORUTA_DUMP_NODES:
     case BORUTA_DUMP_TREE_PTR: {
       std::vector<uint32_t> off(d.D + 2), cnt(d.D + 2);

@@ -42,8 +42,10 @@ struct Dev {
   uint32_t* nd_lcnt;             // [cap][C]
   int64_t* nd_lS;
   uint32_t *lvl_off, *lvl_cnt;   // [D + 2]
-  uint32_t* work;                // [D + 2] node claim counters
+  uint32_t* work;                // [D + 2] per level: number of nodes in `big`
   uint32_t* chunk;               // [kScanBlocks] per-block split counts
+  uint32_t* big;                 // [big_cap] this level's active nodes with > 32 rows
+  void* cand;                    // [big_cap * kItemsPerNode] best candidate per work item
   // ---- importance and Boruta state
   unsigned long long* acc;       // [M][p_aug][6] exact per-tree accumulators
   double* imp;                   // [M][p_aug]
@@ -59,12 +61,17 @@ struct Dev {
 
 constexpr int kScanBlocks = 512;
 constexpr int kSplitThreads = 256;
+constexpr int kItemsPerNode = 16;  // work items (groups of draw slots) per larger node
 
 // launchers (kernels.cu)
 void launch_validate(const Dev& d, cudaStream_t st);
 void launch_shadow(const Dev& d, cudaStream_t st);
 void launch_bootstrap(const Dev& d, int grid, cudaStream_t st);
-void launch_split(const Dev& d, int level, int grid, size_t smem, cudaStream_t st);
+// split.cu: k_split_small (nodes <= 32 rows) then k_split_big on one level
+void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st);
+int split_variant(int kind, int C);
+const void* split_big_ptr(int variant);
+size_t cand_bytes(int variant);
 void launch_children(const Dev& d, int level, cudaStream_t st);
 void launch_treeimp(const Dev& d, int grid, cudaStream_t st);
 void launch_permut(const Dev& d, int grid, cudaStream_t st);
@@ -77,7 +84,6 @@ __host__ __device__ inline size_t split_smem_per_warp(int kind, int C, int B) {
 __host__ __device__ inline size_t split_smem_bytes(int kind, int C, int B) {
   return (kSplitThreads / 32) * split_smem_per_warp(kind, C, B);
 }
-const void* split_kernel_ptr();
 
 void launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                          cudaStream_t st);

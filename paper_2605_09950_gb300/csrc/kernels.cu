@@ -22,12 +22,6 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-__device__ __forceinline__ uint32_t lanemask_lt() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
 // exclusive block scan of one u32 per thread; returns the block total in *total
 __device__ uint32_t block_excl_scan(uint32_t v, uint32_t* total, uint32_t* smem_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -170,12 +164,16 @@ __global__ void k_boot_compact(Dev d) {
       const int i = base + threadIdx.x;
       const uint32_t c = i < d.N ? cnt[i] : 0u;
       const bool in = c > 0u, out = (i < d.N) && c == 0u;
-      wbad |= c > 255u;
+      // entry low byte: classification y << 5 | count (count < 32), regression count (< 256)
+      wbad |= c > (d.kind == 0 ? 31u : 255u);
       uint32_t tin, tout;
       const uint32_t rin = block_excl_scan(in ? 1u : 0u, &tin, sw);
       const uint32_t rout = block_excl_scan(out ? 1u : 0u, &tout, sw);
       if (in) {
-        rows[nin + rin] = (static_cast<uint32_t>(i) << 8) | min(c, 255u);
+        if (d.kind == 0)
+          rows[nin + rin] = (static_cast<uint32_t>(i) << 8) | (static_cast<uint32_t>(d.ycls[i]) << 5) | min(c, 31u);
+        else
+          rows[nin + rin] = (static_cast<uint32_t>(i) << 8) | min(c, 255u);
         if (d.kind == 0) {
           const uint32_t y = d.ycls[i];
 #pragma unroll
@@ -228,535 +226,6 @@ void launch_bootstrap(const Dev& d, int grid, cudaStream_t st) {
   int by = d.M < 4096 ? d.M : 4096;
   k_boot_count<<<dim3(bx, by), 256, 0, st>>>(d);
   k_boot_compact<<<grid, 256, 0, st>>>(d);
-}
-
-// ============================================================ split search
-// Candidate split of a node: left = rows with bin <= `bin` of feature `feat`.
-// Score num/den = (A_L n_R + A_R n_L) / (n_L n_R), A = sum_k c_k^2 (Gini) or
-// S^2 (variance), compared exactly; equal scores go to the lower key =
-// (feature draw slot, or feature index) << 8 | bin.
-struct Cand {
-  U192 num;
-  uint64_t den;
-  uint32_t key;
-  uint32_t nL;
-  uint32_t cL[kMaxClasses];
-  long long SL;
-  int32_t feat;
-  int32_t bin;
-  bool valid;
-};
-
-__device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
-  if (!a.valid) return false;
-  if (!b.valid) return true;
-  const int c = frac_cmp(a.num, a.den, b.num, b.den);
-  if (c != 0) return c > 0;
-  return a.key < b.key;
-}
-
-__device__ __forceinline__ U192 u192_mul(u128 a, uint64_t b) {
-  const u128 lo = static_cast<u128>(static_cast<uint64_t>(a)) * b;
-  const u128 hi = static_cast<u128>(static_cast<uint64_t>(a >> 64)) * b + (lo >> 64);
-  U192 r;
-  r.w[0] = static_cast<uint64_t>(lo);
-  r.w[1] = static_cast<uint64_t>(hi);
-  r.w[2] = static_cast<uint64_t>(hi >> 64);
-  return r;
-}
-
-__device__ __forceinline__ U192 u192_add(const U192& a, const U192& b) {
-  U192 r;
-  u128 s = static_cast<u128>(a.w[0]) + b.w[0];
-  r.w[0] = static_cast<uint64_t>(s);
-  s = static_cast<u128>(a.w[1]) + b.w[1] + (s >> 64);
-  r.w[1] = static_cast<uint64_t>(s);
-  r.w[2] = a.w[2] + b.w[2] + static_cast<uint64_t>(s >> 64);
-  return r;
-}
-
-__device__ __forceinline__ u128 sq_i64(long long v) {
-  const uint64_t m = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
-  return static_cast<u128>(m) * m;
-}
-
-// exact classification candidate from left counts
-__device__ __forceinline__ void cand_class(Cand& c, const uint32_t* cl, const uint32_t* cp, int C,
-                                           uint32_t nL, uint32_t n) {
-  uint64_t AL = 0, AR = 0;
-#pragma unroll
-  for (int k = 0; k < kMaxClasses; ++k) {
-    if (k < C) {
-      const uint64_t l = cl[k], r = cp[k] - cl[k];
-      AL += l * l;
-      AR += r * r;
-      c.cL[k] = cl[k];
-    }
-  }
-  const uint32_t nR = n - nL;
-  c.num = u192_from(static_cast<u128>(AL) * nR + static_cast<u128>(AR) * nL);
-  c.den = static_cast<uint64_t>(nL) * nR;
-  c.nL = nL;
-  c.valid = true;
-}
-
-__device__ __forceinline__ void cand_reg(Cand& c, long long SL, long long SP, uint32_t nL, uint32_t n) {
-  const uint32_t nR = n - nL;
-  c.num = u192_add(u192_mul(sq_i64(SL), nR), u192_mul(sq_i64(SP - SL), nL));
-  c.den = static_cast<uint64_t>(nL) * nR;
-  c.nL = nL;
-  c.SL = SL;
-  c.valid = true;
-}
-
-__device__ __forceinline__ float score_class_f(const uint32_t* cl, const uint32_t* cp, int C,
-                                               uint32_t nL, uint32_t n) {
-  uint64_t AL = 0, AR = 0;
-#pragma unroll
-  for (int k = 0; k < kMaxClasses; ++k) {
-    if (k < C) {
-      const uint64_t l = cl[k], r = cp[k] - cl[k];
-      AL += l * l;
-      AR += r * r;
-    }
-  }
-  return __fdividef(static_cast<float>(AL), static_cast<float>(nL)) +
-         __fdividef(static_cast<float>(AR), static_cast<float>(n - nL));
-}
-
-__device__ __forceinline__ float score_reg_f(long long SL, long long SP, uint32_t nL, uint32_t n) {
-  const float l = static_cast<float>(SL), r = static_cast<float>(SP - SL);
-  return __fdividef(l * l, static_cast<float>(nL)) + __fdividef(r * r, static_cast<float>(n - nL));
-}
-
-// all lanes: out = best of the valid lane candidates (lanes scanned in order)
-__device__ void warp_select(const Cand& mine, Cand& out, int C, bool reg) {
-  unsigned m = __ballot_sync(kFull, mine.valid);
-  out.valid = false;
-  while (m) {
-    const int l = __ffs(m) - 1;
-    m &= m - 1;
-    Cand c;
-    c.num.w[0] = __shfl_sync(kFull, mine.num.w[0], l);
-    c.num.w[1] = __shfl_sync(kFull, mine.num.w[1], l);
-    c.num.w[2] = __shfl_sync(kFull, mine.num.w[2], l);
-    c.den = __shfl_sync(kFull, mine.den, l);
-    c.key = __shfl_sync(kFull, mine.key, l);
-    c.nL = __shfl_sync(kFull, mine.nL, l);
-    c.feat = __shfl_sync(kFull, mine.feat, l);
-    c.bin = __shfl_sync(kFull, mine.bin, l);
-    if (reg) {
-      c.SL = __shfl_sync(kFull, mine.SL, l);
-    } else {
-#pragma unroll
-      for (int k = 0; k < kMaxClasses; ++k)
-        if (k < C) c.cL[k] = __shfl_sync(kFull, mine.cL[k], l);
-    }
-    c.valid = true;
-    if (cand_better(c, out)) out = c;
-  }
-}
-
-// Relative window of the float pre-screen.  The float score of a candidate
-// is within ~2^-21 of its exact value, so every candidate whose exact score
-// is the maximum has a float score above (1 - 2^-12) * (best float score);
-// only those are compared exactly.
-#define SCREEN(m) ((m) - (m) * 0.000244140625f)
-
-struct NodeInfo {
-  int64_t base;  // tree row-buffer offset + segment offset
-  uint32_t len, n;
-  uint32_t cp[kMaxClasses];
-  long long SP;
-};
-
-// Best split of feature `feat` (draw slot `slot`) at the node, warp-wide.
-// Nodes with at most 32 distinct rows: one row per lane, candidates at the
-// bins present.  Larger nodes: warp-private shared-memory histogram, a warp
-// prefix scan over the bins, float screen, exact comparison.
-__device__ void feature_best(const Dev& d, const NodeInfo& nd, const uint32_t* rows, int feat,
-                             uint32_t tkey, uint32_t* hw, Cand& out) {
-  const int lane = threadIdx.x & 31;
-  const bool reg = d.kind != 0;
-  const int C = d.C;
-  const uint8_t* col = d.colptr[feat];
-  Cand mine;
-  mine.valid = false;
-  mine.feat = feat;
-  if (nd.len <= 32u) {
-    const bool v = lane < static_cast<int>(nd.len);
-    const uint32_t e = v ? rows[nd.base + lane] : 0u;
-    const uint32_t row = e >> 8, w = e & 255u;
-    const uint32_t b = v ? col[row] : 0u;
-    const uint32_t y = (v && !reg) ? d.ycls[row] : 0u;
-    const long long yv = (v && reg) ? d.yreg[row] : 0ll;
-    uint32_t cl[kMaxClasses];
-#pragma unroll
-    for (int k = 0; k < kMaxClasses; ++k) cl[k] = 0u;
-    uint32_t nL = 0;
-    long long SL = 0;
-    for (int j = 0; j < static_cast<int>(nd.len); ++j) {
-      const uint32_t bj = __shfl_sync(kFull, b, j), wj = __shfl_sync(kFull, w, j);
-      if (reg) {
-        const long long yj = __shfl_sync(kFull, yv, j);
-        if (bj <= b) {
-          nL += wj;
-          SL += static_cast<long long>(wj) * yj;
-        }
-      } else {
-        const uint32_t yj = __shfl_sync(kFull, y, j);
-        if (bj <= b) {
-          nL += wj;
-#pragma unroll
-          for (int k = 0; k < kMaxClasses; ++k) cl[k] += (yj == static_cast<uint32_t>(k)) ? wj : 0u;
-        }
-      }
-    }
-    const bool ok = v && nL < nd.n;
-    float sf = -1.0f;
-    if (ok) sf = reg ? score_reg_f(SL, nd.SP, nL, nd.n) : score_class_f(cl, nd.cp, C, nL, nd.n);
-    const float mx = warp_max_f(sf);
-    if (mx < 0.0f) {
-      out.valid = false;
-      return;
-    }
-    if (ok && sf >= SCREEN(mx)) {
-      if (reg)
-        cand_reg(mine, SL, nd.SP, nL, nd.n);
-      else
-        cand_class(mine, cl, nd.cp, C, nL, nd.n);
-      mine.bin = static_cast<int32_t>(b);
-      mine.key = (tkey << 8) | b;
-    }
-    warp_select(mine, out, C, reg);
-    return;
-  }
-
-  // ---- dense histogram
-  const int B = d.B;
-  const int bpl = (B + 31) >> 5;  // bins per lane
-  const int b0 = lane * bpl;
-  if (!reg) {
-    for (int i = lane; i < B * C; i += 32) hw[i] = 0u;
-    __syncwarp();
-    for (uint32_t r = lane; r < nd.len; r += 32) {
-      const uint32_t e = rows[nd.base + r];
-      const uint32_t row = e >> 8;
-      atomicAdd(&hw[col[row] * C + d.ycls[row]], e & 255u);
-    }
-    __syncwarp();
-    uint32_t tot[kMaxClasses], pre[kMaxClasses];
-#pragma unroll
-    for (int k = 0; k < kMaxClasses; ++k) tot[k] = 0u;
-    for (int q = 0; q < bpl; ++q) {
-      const int b = b0 + q;
-      if (b < B) {
-#pragma unroll
-        for (int k = 0; k < kMaxClasses; ++k)
-          if (k < C) tot[k] += hw[b * C + k];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kMaxClasses; ++k) pre[k] = (k < C) ? warp_excl_scan_u32(tot[k], lane) : 0u;
-    // pass 1: float scores
-    float sf[8];
-    float lmax = -1.0f;
-    uint32_t cum[kMaxClasses];
-#pragma unroll
-    for (int k = 0; k < kMaxClasses; ++k) cum[k] = pre[k];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      sf[q] = -1.0f;
-      const int b = b0 + q;
-      if (q < bpl && b < B - 1) {
-        uint32_t nL = 0;
-#pragma unroll
-        for (int k = 0; k < kMaxClasses; ++k)
-          if (k < C) {
-            cum[k] += hw[b * C + k];
-            nL += cum[k];
-          }
-        if (nL > 0u && nL < nd.n) {
-          sf[q] = score_class_f(cum, nd.cp, C, nL, nd.n);
-          lmax = fmaxf(lmax, sf[q]);
-        }
-      }
-    }
-    const float mx = warp_max_f(lmax);
-    if (mx < 0.0f) {
-      out.valid = false;
-      return;
-    }
-    const float thr = SCREEN(mx);
-    // pass 2: exact among the contenders (bins ascending: first of equals kept)
-#pragma unroll
-    for (int k = 0; k < kMaxClasses; ++k) cum[k] = pre[k];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int b = b0 + q;
-      if (q < bpl && b < B - 1) {
-        uint32_t nL = 0;
-#pragma unroll
-        for (int k = 0; k < kMaxClasses; ++k)
-          if (k < C) {
-            cum[k] += hw[b * C + k];
-            nL += cum[k];
-          }
-        if (sf[q] >= 0.0f && sf[q] >= thr) {
-          Cand c;
-          cand_class(c, cum, nd.cp, C, nL, nd.n);
-          c.feat = feat;
-          c.bin = b;
-          c.key = (tkey << 8) | static_cast<uint32_t>(b);
-          if (cand_better(c, mine)) mine = c;
-        }
-      }
-    }
-  } else {
-    uint32_t* hn = hw;
-    unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + ((B + 1) & ~1));
-    for (int i = lane; i < B; i += 32) {
-      hn[i] = 0u;
-      hs[i] = 0ull;
-    }
-    __syncwarp();
-    for (uint32_t r = lane; r < nd.len; r += 32) {
-      const uint32_t e = rows[nd.base + r];
-      const uint32_t row = e >> 8, w = e & 255u;
-      const uint32_t b = col[row];
-      atomicAdd(&hn[b], w);
-      atomicAdd(&hs[b], static_cast<unsigned long long>(static_cast<long long>(w) * d.yreg[row]));
-    }
-    __syncwarp();
-    uint32_t tn = 0;
-    long long ts = 0;
-    for (int q = 0; q < bpl; ++q) {
-      const int b = b0 + q;
-      if (b < B) {
-        tn += hn[b];
-        ts += static_cast<long long>(hs[b]);
-      }
-    }
-    const uint32_t pn = warp_excl_scan_u32(tn, lane);
-    const long long ps = warp_excl_scan_i64(ts, lane);
-    float sf[8];
-    float lmax = -1.0f;
-    uint32_t cn = pn;
-    long long cs = ps;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      sf[q] = -1.0f;
-      const int b = b0 + q;
-      if (q < bpl && b < B - 1) {
-        cn += hn[b];
-        cs += static_cast<long long>(hs[b]);
-        if (cn > 0u && cn < nd.n) {
-          sf[q] = score_reg_f(cs, nd.SP, cn, nd.n);
-          lmax = fmaxf(lmax, sf[q]);
-        }
-      }
-    }
-    const float mx = warp_max_f(lmax);
-    if (mx < 0.0f) {
-      out.valid = false;
-      return;
-    }
-    const float thr = SCREEN(mx);
-    cn = pn;
-    cs = ps;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int b = b0 + q;
-      if (q < bpl && b < B - 1) {
-        cn += hn[b];
-        cs += static_cast<long long>(hs[b]);
-        if (sf[q] >= 0.0f && sf[q] >= thr) {
-          Cand c;
-          cand_reg(c, cs, nd.SP, cn, nd.n);
-          c.feat = feat;
-          c.bin = b;
-          c.key = (tkey << 8) | static_cast<uint32_t>(b);
-          if (cand_better(c, mine)) mine = c;
-        }
-      }
-    }
-  }
-  warp_select(mine, out, C, reg);
-}
-
-// Exact impurity decrease of the chosen split:
-//   delta = num/den - A_P/n_P = (num*n_P - A_P*den) / (den*n_P), rounded as
-//   RN(numerator) / RN(denominator).  Returns false if delta <= 0.
-__device__ bool split_delta(const Cand& c, const NodeInfo& nd, int C, bool reg, int precision,
-                            double* delta) {
-  u128 AP;
-  if (reg) {
-    AP = sq_i64(nd.SP);
-  } else {
-    AP = 0;
-    for (int k = 0; k < C; ++k) AP += static_cast<u128>(static_cast<uint64_t>(nd.cp[k]) * nd.cp[k]);
-  }
-  uint64_t lhs[4], rhs[4];
-  mul192x64(c.num, nd.n, lhs);
-  const U192 ap = u192_from(AP);
-  mul192x64(ap, c.den, rhs);
-  if (cmp_limbs4(lhs, rhs) <= 0) return false;
-  uint64_t dn[4];
-  uint64_t borrow = 0;
-  for (int i = 0; i < 4; ++i) {
-    const uint64_t a = lhs[i], b = rhs[i];
-    const uint64_t t = a - b;
-    const uint64_t b1 = a < b;
-    dn[i] = t - borrow;
-    const uint64_t b2 = t < borrow;
-    borrow = b1 | b2;
-  }
-  const u128 dd = static_cast<u128>(c.den) * nd.n;
-  const uint64_t dl[2] = {static_cast<uint64_t>(dd), static_cast<uint64_t>(dd >> 64)};
-  if (precision == 0) {
-    *delta = limbs_to_double(dn, 4, 0) / limbs_to_double(dl, 2, 0);
-  } else {
-    *delta = static_cast<double>(__fdiv_rn(limbs_to_float(dn, 4, 0), limbs_to_float(dl, 2, 0)));
-  }
-  return true;
-}
-
-// One CTA per node (claimed dynamically).  Warps take the node's feature
-// draw slots in turn; the CTA keeps the best candidate, records the split,
-// adds its impurity decrease to the tree's TreeImp accumulator and
-// partitions the node's rows (left rows first, right rows last, both in
-// order) into the next level's buffer.
-__global__ void __launch_bounds__(kSplitThreads) k_split(Dev d, int level) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ Perm sperm;
-  __shared__ NodeInfo snd;
-  __shared__ Cand swarp[kSplitThreads / 32];
-  __shared__ uint32_t snode, ssplit, swl[kSplitThreads / 32], swr[kSplitThreads / 32];
-  __shared__ int sact;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const bool reg = d.kind != 0;
-  const int C = d.C;
-  uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, C, d.B) / 4);
-  const uint32_t* rows_in = d.rows[level & 1];
-  uint32_t* rows_out = d.rows[(level & 1) ^ 1];
-  const uint32_t lcount = d.lvl_cnt[level], loff = d.lvl_off[level];
-
-  for (;;) {
-    if (threadIdx.x == 0) snode = atomicAdd(&d.work[level], 1u);
-    __syncthreads();
-    const uint32_t idx = snode;
-    if (idx >= lcount) break;
-    const uint32_t k = loff + idx;
-    if (threadIdx.x == 0) {
-      NodeInfo nd;
-      const uint32_t tau = d.nd_tree[k];
-      nd.base = static_cast<int64_t>(tau) * d.N + d.nd_seg[k];
-      nd.len = d.nd_len[k];
-      nd.n = d.nd_n[k];
-      nd.SP = 0;
-      bool pure = false;
-      if (!reg) {
-        for (int c = 0; c < kMaxClasses; ++c) {
-          nd.cp[c] = c < C ? d.nd_cnt[static_cast<int64_t>(k) * C + c] : 0u;
-          pure |= (c < C) && nd.cp[c] == nd.n;
-        }
-      } else {
-        nd.SP = d.nd_S[k];
-      }
-      snd = nd;
-      const bool act = level < d.D && nd.len >= 2u && !pure;
-      sact = act;
-      if (act)
-        perm_init(sperm, static_cast<uint32_t>(d.p_aug), d.seed, d.nd_heap[k], unit_word(d.t, tau),
-                  purpose_word(kPurposeMtry, d.job));
-      else
-        d.nd_split[k] = kLeaf;
-    }
-    __syncthreads();
-    if (!sact) continue;
-    const NodeInfo nd = snd;
-    const Perm P = sperm;
-
-    Cand best;
-    best.valid = false;
-    for (int slot = warp; slot < d.mtry; slot += nw) {
-      const int f = static_cast<int>(perm_apply(P, static_cast<uint32_t>(slot)));
-      const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(slot) : static_cast<uint32_t>(f);
-      Cand c;
-      feature_best(d, nd, rows_in, f, tkey, hw, c);
-      if (cand_better(c, best)) best = c;
-    }
-    if (lane == 0) swarp[warp] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      Cand b = swarp[0];
-      for (int w = 1; w < nw; ++w)
-        if (cand_better(swarp[w], b)) b = swarp[w];
-      double delta = 0.0;
-      uint32_t sp = kLeaf;
-      if (b.valid && split_delta(b, nd, C, reg, d.precision, &delta)) {
-        sp = (static_cast<uint32_t>(b.feat) << 8) | static_cast<uint32_t>(b.bin);
-        d.nd_delta[k] = delta;
-        d.nd_ln[k] = b.nL;
-        if (reg)
-          d.nd_lS[k] = b.SL;
-        else
-          for (int c = 0; c < C; ++c) d.nd_lcnt[static_cast<int64_t>(k) * C + c] = b.cL[c];
-        uint64_t v[kFixLimbs];
-        if (!fix_from_double(delta, v)) atomicOr(&d.status[0], kErrAcc);
-        if (!d.permut)
-          fix_atomic_add(d.acc + (static_cast<int64_t>(d.nd_tree[k]) * d.p_aug + b.feat) * kFixLimbs, v);
-      }
-      d.nd_split[k] = sp;
-      ssplit = sp;
-      const unsigned long long ybytes = reg ? 8ull : 1ull;
-      atomicAdd(&d.counters[0], static_cast<unsigned long long>(nd.len) * d.mtry +
-                                    static_cast<unsigned long long>(nd.len) * (4ull + ybytes) +
-                                    (sp != kLeaf ? static_cast<unsigned long long>(nd.len) * 5ull : 0ull));
-    }
-    __syncthreads();
-    const uint32_t sp = ssplit;
-    if (sp == kLeaf) continue;
-
-    // ---- stable partition into rows_out[base .. base+len)
-    const uint8_t* col = d.colptr[sp >> 8];
-    const uint32_t thr = sp & 255u;
-    uint32_t lbase = 0, rbase = 0;
-    for (uint32_t off = 0; off < nd.len; off += blockDim.x) {
-      const uint32_t r = off + threadIdx.x;
-      const bool v = r < nd.len;
-      const uint32_t e = v ? rows_in[nd.base + r] : 0u;
-      const bool gl = v && col[e >> 8] <= thr;
-      const bool gr = v && !gl;
-      const unsigned bl = __ballot_sync(kFull, gl), br = __ballot_sync(kFull, gr);
-      if (lane == 0) {
-        swl[warp] = __popc(bl);
-        swr[warp] = __popc(br);
-      }
-      __syncthreads();
-      uint32_t pl = 0, pr = 0, tl = 0, tr = 0;
-      for (int w = 0; w < nw; ++w) {
-        if (w < warp) {
-          pl += swl[w];
-          pr += swr[w];
-        }
-        tl += swl[w];
-        tr += swr[w];
-      }
-      if (gl) rows_out[nd.base + lbase + pl + __popc(bl & lanemask_lt())] = e;
-      if (gr) rows_out[nd.base + nd.len - 1u - (rbase + pr + __popc(br & lanemask_lt()))] = e;
-      lbase += tl;
-      rbase += tr;
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) d.nd_lrows[k] = lbase;
-  }
-}
-
-const void* split_kernel_ptr() { return reinterpret_cast<const void*>(&k_split); }
-
-void launch_split(const Dev& d, int level, int grid, size_t smem, cudaStream_t st) {
-  k_split<<<grid, kSplitThreads, smem, st>>>(d, level);
 }
 
 // ============================================================ next level

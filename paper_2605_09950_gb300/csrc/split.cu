@@ -1,0 +1,713 @@
+// Split search of one tree level (all trees at once): per-node feature
+// sample, histograms, exact best-split scan, impurity decrease into the
+// TreeImp accumulators (Alg. 2) and the stable row partition.
+//
+// Two kernels share a level:
+//   k_split_small  one warp per node with at most 32 distinct rows: one row
+//                  per lane, candidate thresholds at the bins present, left
+//                  counts from a warp-wide compare loop (no histogram);
+//   k_items        larger nodes, one warp per (node, group of draw slots):
+//                  a warp-private shared-memory histogram per feature from
+//                  batched gathers, a warp prefix scan over the bins, the
+//                  best candidate of the group;
+//   k_finalize     one warp per larger node: exact argmax over its groups,
+//                  the split record, and the stable row partition.
+// Candidate (f, b): rows with bin <= b go left.  Score num/den =
+// (A_L n_R + A_R n_L) / (n_L n_R) with A = sum_k c_k^2 (Gini) or S^2
+// (variance); scores are compared exactly (256-bit cross products) after a
+// float pre-screen; equal scores go to the lower key = (draw slot, or
+// feature index) << 8 | bin.
+#include <cstdint>
+
+#include "engine.cuh"
+
+namespace bgb {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Row entries: row << 8 | low byte.  Classification: low byte = y << 5 | w
+// (label < 8, bootstrap count < 32); regression: low byte = w (< 256).
+template <int KIND>
+__device__ __forceinline__ uint32_t ent_w(uint32_t e) {
+  return KIND == 0 ? (e & 31u) : (e & 255u);
+}
+__device__ __forceinline__ uint32_t ent_y(uint32_t e) { return (e >> 5) & 7u; }
+
+template <int CM>
+struct Cand {
+  U192 num;
+  uint64_t den;
+  uint32_t key;
+  uint32_t nL;
+  uint32_t cL[CM];
+  long long SL;
+  int32_t feat;
+  int32_t bin;
+  bool valid;
+};
+
+template <int CM>
+__device__ __forceinline__ bool better(const Cand<CM>& a, const Cand<CM>& b) {
+  if (!a.valid) return false;
+  if (!b.valid) return true;
+  const int c = frac_cmp(a.num, a.den, b.num, b.den);
+  if (c != 0) return c > 0;
+  return a.key < b.key;
+}
+
+__device__ __forceinline__ U192 u192_mul(u128 a, uint64_t b) {
+  const u128 lo = static_cast<u128>(static_cast<uint64_t>(a)) * b;
+  const u128 hi = static_cast<u128>(static_cast<uint64_t>(a >> 64)) * b + (lo >> 64);
+  U192 r;
+  r.w[0] = static_cast<uint64_t>(lo);
+  r.w[1] = static_cast<uint64_t>(hi);
+  r.w[2] = static_cast<uint64_t>(hi >> 64);
+  return r;
+}
+
+__device__ __forceinline__ U192 u192_add(const U192& a, const U192& b) {
+  U192 r;
+  u128 s = static_cast<u128>(a.w[0]) + b.w[0];
+  r.w[0] = static_cast<uint64_t>(s);
+  s = static_cast<u128>(a.w[1]) + b.w[1] + (s >> 64);
+  r.w[1] = static_cast<uint64_t>(s);
+  r.w[2] = a.w[2] + b.w[2] + static_cast<uint64_t>(s >> 64);
+  return r;
+}
+
+__device__ __forceinline__ u128 sq_i64(long long v) {
+  const uint64_t m = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+  return static_cast<u128>(m) * m;
+}
+
+template <int CM>
+struct NodeInfo {
+  int64_t base;  // tree row-buffer offset + segment offset
+  uint32_t len, n;
+  uint32_t cp[CM];
+  long long SP;
+};
+
+// ---- scores
+template <int CM>
+__device__ __forceinline__ float score_class_f(const uint32_t* cl, const uint32_t* cp, int C, uint32_t nL,
+                                               uint32_t n) {
+  uint64_t AL = 0, AR = 0;
+#pragma unroll
+  for (int k = 0; k < CM; ++k)
+    if (k < C) {
+      const uint64_t l = cl[k], r = cp[k] - cl[k];
+      AL += l * l;
+      AR += r * r;
+    }
+  return __fdividef(static_cast<float>(AL), static_cast<float>(nL)) +
+         __fdividef(static_cast<float>(AR), static_cast<float>(n - nL));
+}
+
+__device__ __forceinline__ float score_reg_f(long long SL, long long SP, uint32_t nL, uint32_t n) {
+  const float l = static_cast<float>(SL), r = static_cast<float>(SP - SL);
+  return __fdividef(l * l, static_cast<float>(nL)) + __fdividef(r * r, static_cast<float>(n - nL));
+}
+
+template <int CM>
+__device__ __forceinline__ void make_class(Cand<CM>& c, const uint32_t* cl, const uint32_t* cp, int C,
+                                           uint32_t nL, uint32_t n) {
+  uint64_t AL = 0, AR = 0;
+#pragma unroll
+  for (int k = 0; k < CM; ++k) {
+    c.cL[k] = k < C ? cl[k] : 0u;
+    if (k < C) {
+      const uint64_t l = cl[k], r = cp[k] - cl[k];
+      AL += l * l;
+      AR += r * r;
+    }
+  }
+  const uint32_t nR = n - nL;
+  c.num = u192_from(static_cast<u128>(AL) * nR + static_cast<u128>(AR) * nL);
+  c.den = static_cast<uint64_t>(nL) * nR;
+  c.nL = nL;
+  c.SL = 0;
+  c.valid = true;
+}
+
+template <int CM>
+__device__ __forceinline__ void make_reg(Cand<CM>& c, long long SL, long long SP, uint32_t nL, uint32_t n) {
+  const uint32_t nR = n - nL;
+  c.num = u192_add(u192_mul(sq_i64(SL), nR), u192_mul(sq_i64(SP - SL), nL));
+  c.den = static_cast<uint64_t>(nL) * nR;
+  c.nL = nL;
+  c.SL = SL;
+#pragma unroll
+  for (int k = 0; k < CM; ++k) c.cL[k] = 0u;
+  c.valid = true;
+}
+
+// Relative window of the float pre-screen.  A float score is within ~2^-21
+// of the exact score, so every candidate whose exact score is the maximum
+// has a float score above (1 - 2^-12) * (best float score); only those are
+// compared exactly.
+__device__ __forceinline__ float screen(float m) { return m - m * 0.000244140625f; }
+
+// all lanes: out = best of the lane candidates flagged valid
+template <int KIND, int CM>
+__device__ void warp_select(const Cand<CM>& mine, Cand<CM>& out) {
+  unsigned m = __ballot_sync(kFull, mine.valid);
+  out.valid = false;
+  while (m) {
+    const int l = __ffs(m) - 1;
+    m &= m - 1;
+    Cand<CM> c;
+    c.num.w[0] = __shfl_sync(kFull, mine.num.w[0], l);
+    c.num.w[1] = __shfl_sync(kFull, mine.num.w[1], l);
+    c.num.w[2] = __shfl_sync(kFull, mine.num.w[2], l);
+    c.den = __shfl_sync(kFull, mine.den, l);
+    c.key = __shfl_sync(kFull, mine.key, l);
+    c.nL = __shfl_sync(kFull, mine.nL, l);
+    c.feat = __shfl_sync(kFull, mine.feat, l);
+    c.bin = __shfl_sync(kFull, mine.bin, l);
+    if (KIND == 1) {
+      c.SL = __shfl_sync(kFull, mine.SL, l);
+#pragma unroll
+      for (int k = 0; k < CM; ++k) c.cL[k] = 0u;
+    } else {
+      c.SL = 0;
+#pragma unroll
+      for (int k = 0; k < CM; ++k) c.cL[k] = __shfl_sync(kFull, mine.cL[k], l);
+    }
+    c.valid = true;
+    if (better(c, out)) out = c;
+  }
+}
+
+// Exact impurity decrease of the chosen split:
+//   delta = num/den - A_P/n_P = (num*n_P - A_P*den) / (den*n_P), rounded as
+//   RN(numerator) / RN(denominator) in the working precision.
+template <int KIND, int CM>
+__device__ bool split_delta(const Cand<CM>& c, const NodeInfo<CM>& nd, int C, int precision, double* delta) {
+  u128 AP = 0;
+  if (KIND == 1) {
+    AP = sq_i64(nd.SP);
+  } else {
+#pragma unroll
+    for (int k = 0; k < CM; ++k)
+      if (k < C) AP += static_cast<u128>(static_cast<uint64_t>(nd.cp[k]) * nd.cp[k]);
+  }
+  uint64_t lhs[4], rhs[4];
+  mul192x64(c.num, nd.n, lhs);
+  mul192x64(u192_from(AP), c.den, rhs);
+  if (cmp_limbs4(lhs, rhs) <= 0) return false;
+  uint64_t dn[4];
+  uint64_t borrow = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint64_t a = lhs[i], b = rhs[i];
+    const uint64_t t = a - b;
+    const uint64_t b1 = a < b;
+    dn[i] = t - borrow;
+    const uint64_t b2 = t < borrow;
+    borrow = b1 | b2;
+  }
+  const u128 dd = static_cast<u128>(c.den) * nd.n;
+  const uint64_t dl[2] = {static_cast<uint64_t>(dd), static_cast<uint64_t>(dd >> 64)};
+  if (precision == 0)
+    *delta = limbs_to_double(dn, 4, 0) / limbs_to_double(dl, 2, 0);
+  else
+    *delta = static_cast<double>(__fdiv_rn(limbs_to_float(dn, 4, 0), limbs_to_float(dl, 2, 0)));
+  return true;
+}
+
+// Records the split of node k (or marks it a leaf); one thread.
+template <int KIND, int CM>
+__device__ uint32_t commit_split(const Dev& d, uint32_t k, const Cand<CM>& b, const NodeInfo<CM>& nd) {
+  double delta = 0.0;
+  uint32_t sp = kLeaf;
+  if (b.valid && split_delta<KIND, CM>(b, nd, d.C, d.precision, &delta)) {
+    sp = (static_cast<uint32_t>(b.feat) << 8) | static_cast<uint32_t>(b.bin);
+    d.nd_delta[k] = delta;
+    d.nd_ln[k] = b.nL;
+    if (KIND == 1) {
+      d.nd_lS[k] = b.SL;
+    } else {
+#pragma unroll
+      for (int c = 0; c < CM; ++c)
+        if (c < d.C) d.nd_lcnt[static_cast<int64_t>(k) * d.C + c] = b.cL[c];
+    }
+    if (!d.permut) {  // Alg. 2: this node's gain x samples, summed exactly per (tree, feature)
+      uint64_t v[kFixLimbs];
+      if (!fix_from_double(delta, v))
+        atomicOr(&d.status[0], kErrAcc);
+      else
+        fix_atomic_add(d.acc + (static_cast<int64_t>(d.nd_tree[k]) * d.p_aug + b.feat) * kFixLimbs, v);
+    }
+  }
+  d.nd_split[k] = sp;
+  return sp;
+}
+
+template <int KIND, int CM>
+__device__ bool load_node(const Dev& d, uint32_t k, int level, NodeInfo<CM>& nd) {
+  const uint32_t tau = d.nd_tree[k];
+  nd.base = static_cast<int64_t>(tau) * d.N + d.nd_seg[k];
+  nd.len = d.nd_len[k];
+  nd.n = d.nd_n[k];
+  nd.SP = 0;
+  bool pure = false;
+#pragma unroll
+  for (int c = 0; c < CM; ++c) {
+    nd.cp[c] = 0u;
+    if (KIND == 0 && c < d.C) {
+      nd.cp[c] = d.nd_cnt[static_cast<int64_t>(k) * d.C + c];
+      pure |= nd.cp[c] == nd.n;
+    }
+  }
+  if (KIND == 1) nd.SP = d.nd_S[k];
+  return level < d.D && nd.len >= 2u && !pure;
+}
+
+// ============================================================ small nodes
+// Best split of one feature for a node of <= 32 rows, one row per lane.
+template <int KIND, int CM>
+__device__ void small_feature(const NodeInfo<CM>& nd, int C, bool v, uint32_t b, uint32_t w, uint32_t y,
+                              long long yv, int feat, uint32_t tkey, Cand<CM>& out) {
+  uint32_t cl[CM];
+#pragma unroll
+  for (int k = 0; k < CM; ++k) cl[k] = 0u;
+  uint32_t nL = 0;
+  long long SL = 0;
+  for (int j = 0; j < static_cast<int>(nd.len); ++j) {
+    const uint32_t bj = __shfl_sync(kFull, b, j), wj = __shfl_sync(kFull, w, j);
+    if (KIND == 1) {
+      const long long yj = __shfl_sync(kFull, yv, j);
+      if (bj <= b) {
+        nL += wj;
+        SL += static_cast<long long>(wj) * yj;
+      }
+    } else {
+      const uint32_t yj = __shfl_sync(kFull, y, j);
+      if (bj <= b) {
+        nL += wj;
+#pragma unroll
+        for (int k = 0; k < CM; ++k) cl[k] += (yj == static_cast<uint32_t>(k)) ? wj : 0u;
+      }
+    }
+  }
+  const bool ok = v && nL < nd.n;
+  float sf = -1.0f;
+  if (ok) sf = KIND == 1 ? score_reg_f(SL, nd.SP, nL, nd.n) : score_class_f<CM>(cl, nd.cp, C, nL, nd.n);
+  const float mx = warp_max_f(sf);
+  out.valid = false;
+  if (mx < 0.0f) return;
+  Cand<CM> mine;
+  mine.valid = false;
+  if (ok && sf >= screen(mx)) {
+    if (KIND == 1)
+      make_reg<CM>(mine, SL, nd.SP, nL, nd.n);
+    else
+      make_class<CM>(mine, cl, nd.cp, C, nL, nd.n);
+    mine.feat = feat;
+    mine.bin = static_cast<int32_t>(b);
+    mine.key = (tkey << 8) | b;
+  }
+  warp_select<KIND, CM>(mine, out);
+}
+
+template <int KIND, int CM>
+__global__ void __launch_bounds__(256) k_split_small(Dev d, int level) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t* rows_in = d.rows[level & 1];
+  uint32_t* rows_out = d.rows[(level & 1) ^ 1];
+  const uint32_t lcount = d.lvl_cnt[level], loff = d.lvl_off[level];
+  const int C = d.C;
+  unsigned long long bytes = 0;
+  for (uint32_t idx = gwarp; idx < lcount; idx += nwarps) {
+    const uint32_t k = loff + idx;
+    NodeInfo<CM> nd;
+    const bool act = load_node<KIND, CM>(d, k, level, nd);
+    if (!act) {
+      if (lane == 0) d.nd_split[k] = kLeaf;
+      continue;
+    }
+    if (nd.len > 32u) {  // handled by k_items / k_finalize
+      if (lane == 0) d.big[atomicAdd(&d.work[level], 1u)] = k;
+      continue;
+    }
+    Perm P;
+    perm_init(P, static_cast<uint32_t>(d.p_aug), d.seed, d.nd_heap[k], unit_word(d.t, d.nd_tree[k]),
+              purpose_word(kPurposeMtry, d.job));
+    const bool v = lane < static_cast<int>(nd.len);
+    const uint32_t e = v ? rows_in[nd.base + lane] : 0u;
+    const uint32_t row = e >> 8, w = v ? ent_w<KIND>(e) : 0u;
+    const uint32_t y = KIND == 0 ? ent_y(e) : 0u;
+    const long long yv = (KIND == 1 && v) ? d.yreg[row] : 0ll;
+    Cand<CM> best;
+    best.valid = false;
+    for (int r0 = 0; r0 < d.mtry; r0 += 32) {
+      const int ns = min(32, d.mtry - r0);
+      const uint32_t myf = lane < ns ? perm_apply(P, static_cast<uint32_t>(r0 + lane)) : 0u;
+      for (int j = 0; j < ns; j += 4) {
+        int fq[4];
+        uint32_t bq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fq[q] = static_cast<int>(__shfl_sync(kFull, myf, min(j + q, ns - 1)));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bq[q] = (v && j + q < ns) ? d.colptr[fq[q]][row] : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (j + q < ns) {
+            const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(r0 + j + q) : static_cast<uint32_t>(fq[q]);
+            Cand<CM> c;
+            small_feature<KIND, CM>(nd, C, v, bq[q], w, y, yv, fq[q], tkey, c);
+            if (better(c, best)) best = c;
+          }
+        }
+      }
+    }
+    uint32_t sp = 0;
+    if (lane == 0) sp = commit_split<KIND, CM>(d, k, best, nd);
+    sp = __shfl_sync(kFull, sp, 0);
+    bytes += static_cast<unsigned long long>(nd.len) * (d.mtry + 4ull + (KIND ? 8ull : 0ull));
+    if (sp == kLeaf) continue;
+    // stable partition: left rows in order, then right rows in order
+    const uint32_t bs = v ? d.colptr[sp >> 8][row] : 0u;
+    const bool gl = v && bs <= (sp & 255u), gr = v && !gl;
+    const unsigned bl = __ballot_sync(kFull, gl), br = __ballot_sync(kFull, gr);
+    const uint32_t nl = __popc(bl);
+    if (gl) rows_out[nd.base + __popc(bl & lanemask_lt())] = e;
+    if (gr) rows_out[nd.base + nl + __popc(br & lanemask_lt())] = e;
+    if (lane == 0) d.nd_lrows[k] = nl;
+    bytes += static_cast<unsigned long long>(nd.len) * 5ull;
+  }
+  if (lane == 0 && bytes) atomicAdd(&d.counters[0], bytes);
+}
+
+// ============================================================ larger nodes
+// Best split of one feature of a node with > 32 rows, warp-wide, from a
+// warp-private histogram.  Rows are gathered 8 per lane per pass so that 8
+// independent loads per lane are in flight.
+template <int KIND, int CM>
+__device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* rows, int feat, uint32_t tkey,
+                              uint32_t* hw, Cand<CM>& out) {
+  const int lane = threadIdx.x & 31;
+  const int C = d.C, B = d.B;
+  const uint8_t* col = d.colptr[feat];
+  constexpr int kBatch = 8;
+  uint32_t* hn = hw;
+  unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + ((B + 1) & ~1));
+  if (KIND == 0) {
+    for (int i = lane; i < B * C; i += 32) hw[i] = 0u;
+  } else {
+    for (int i = lane; i < B; i += 32) {
+      hn[i] = 0u;
+      hs[i] = 0ull;
+    }
+  }
+  __syncwarp();
+  for (uint32_t r0 = 0; r0 < nd.len; r0 += 32 * kBatch) {
+    uint32_t e[kBatch];
+    uint32_t b[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const uint32_t r = r0 + q * 32 + lane;
+      e[q] = r < nd.len ? rows[nd.base + r] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const uint32_t r = r0 + q * 32 + lane;
+      b[q] = r < nd.len ? col[e[q] >> 8] : 0u;
+    }
+    if (KIND == 0) {
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q)
+        if (r0 + q * 32 + lane < nd.len) atomicAdd(&hw[b[q] * C + ent_y(e[q])], ent_w<0>(e[q]));
+    } else {
+      long long yq[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        const uint32_t r = r0 + q * 32 + lane;
+        yq[q] = r < nd.len ? d.yreg[e[q] >> 8] : 0ll;
+      }
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q)
+        if (r0 + q * 32 + lane < nd.len) {
+          const uint32_t w = ent_w<1>(e[q]);
+          atomicAdd(&hn[b[q]], w);
+          atomicAdd(&hs[b[q]], static_cast<unsigned long long>(static_cast<long long>(w) * yq[q]));
+        }
+    }
+  }
+  __syncwarp();
+  const int bpl = (B + 31) >> 5;  // bins per lane (<= 8)
+  const int b0 = lane * bpl;
+  Cand<CM> mine;
+  mine.valid = false;
+  float sf[8];
+  float lmax = -1.0f;
+  if (KIND == 0) {
+    uint32_t pre[CM], cum[CM];
+#pragma unroll
+    for (int k = 0; k < CM; ++k) pre[k] = 0u;
+    for (int q = 0; q < bpl; ++q) {
+      const int bb = b0 + q;
+      if (bb < B) {
+#pragma unroll
+        for (int k = 0; k < CM; ++k)
+          if (k < C) pre[k] += hw[bb * C + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CM; ++k) {
+      pre[k] = warp_excl_scan_u32(pre[k], lane);
+      cum[k] = pre[k];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sf[q] = -1.0f;
+      const int bb = b0 + q;
+      if (q < bpl && bb < B - 1) {
+        uint32_t nL = 0;
+#pragma unroll
+        for (int k = 0; k < CM; ++k)
+          if (k < C) {
+            cum[k] += hw[bb * C + k];
+            nL += cum[k];
+          }
+        if (nL > 0u && nL < nd.n) {
+          sf[q] = score_class_f<CM>(cum, nd.cp, C, nL, nd.n);
+          lmax = fmaxf(lmax, sf[q]);
+        }
+      }
+    }
+    const float mx = warp_max_f(lmax);
+    out.valid = false;
+    if (mx < 0.0f) return;
+    const float thr = screen(mx);
+#pragma unroll
+    for (int k = 0; k < CM; ++k) cum[k] = pre[k];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int bb = b0 + q;
+      if (q < bpl && bb < B - 1) {
+        uint32_t nL = 0;
+#pragma unroll
+        for (int k = 0; k < CM; ++k)
+          if (k < C) {
+            cum[k] += hw[bb * C + k];
+            nL += cum[k];
+          }
+        if (sf[q] >= 0.0f && sf[q] >= thr) {
+          Cand<CM> c;
+          make_class<CM>(c, cum, nd.cp, C, nL, nd.n);
+          c.feat = feat;
+          c.bin = bb;
+          c.key = (tkey << 8) | static_cast<uint32_t>(bb);
+          if (better(c, mine)) mine = c;
+        }
+      }
+    }
+  } else {
+    uint32_t tn = 0;
+    long long ts = 0;
+    for (int q = 0; q < bpl; ++q) {
+      const int bb = b0 + q;
+      if (bb < B) {
+        tn += hn[bb];
+        ts += static_cast<long long>(hs[bb]);
+      }
+    }
+    const uint32_t pn = warp_excl_scan_u32(tn, lane);
+    const long long ps = warp_excl_scan_i64(ts, lane);
+    uint32_t cn = pn;
+    long long cs = ps;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sf[q] = -1.0f;
+      const int bb = b0 + q;
+      if (q < bpl && bb < B - 1) {
+        cn += hn[bb];
+        cs += static_cast<long long>(hs[bb]);
+        if (cn > 0u && cn < nd.n) {
+          sf[q] = score_reg_f(cs, nd.SP, cn, nd.n);
+          lmax = fmaxf(lmax, sf[q]);
+        }
+      }
+    }
+    const float mx = warp_max_f(lmax);
+    out.valid = false;
+    if (mx < 0.0f) return;
+    const float thr = screen(mx);
+    cn = pn;
+    cs = ps;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int bb = b0 + q;
+      if (q < bpl && bb < B - 1) {
+        cn += hn[bb];
+        cs += static_cast<long long>(hs[bb]);
+        if (sf[q] >= 0.0f && sf[q] >= thr) {
+          Cand<CM> c;
+          make_reg<CM>(c, cs, nd.SP, cn, nd.n);
+          c.feat = feat;
+          c.bin = bb;
+          c.key = (tkey << 8) | static_cast<uint32_t>(bb);
+          if (better(c, mine)) mine = c;
+        }
+      }
+    }
+  }
+  warp_select<KIND, CM>(mine, out);
+}
+
+// Work items of one level's larger nodes: (node, group of G consecutive
+// draw slots), one warp each, spread round-robin over all warps so that a
+// few very large nodes (shallow levels) still occupy the whole GPU.  Each
+// item writes its best candidate; k_finalize reduces them per node.
+template <int KIND, int CM>
+__global__ void __launch_bounds__(kSplitThreads, 2) k_items(Dev d, int level) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t* rows_in = d.rows[level & 1];
+  const uint32_t nbig = d.work[level];
+  const int G = (d.mtry + kItemsPerNode - 1) / kItemsPerNode;
+  const int ipn = (d.mtry + G - 1) / G;
+  Cand<CM>* out = reinterpret_cast<Cand<CM>*>(d.cand);
+  const uint64_t total = static_cast<uint64_t>(nbig) * ipn;
+  for (uint64_t it = gwarp; it < total; it += nwarps) {
+    const uint32_t rank = static_cast<uint32_t>(it / ipn);
+    const int part = static_cast<int>(it - static_cast<uint64_t>(rank) * ipn);
+    const uint32_t k = d.big[rank];
+    NodeInfo<CM> nd;
+    load_node<KIND, CM>(d, k, level, nd);
+    Perm P;
+    perm_init(P, static_cast<uint32_t>(d.p_aug), d.seed, d.nd_heap[k], unit_word(d.t, d.nd_tree[k]),
+              purpose_word(kPurposeMtry, d.job));
+    Cand<CM> best;
+    best.valid = false;
+    const int s1 = min(d.mtry, (part + 1) * G);
+    for (int slot = part * G; slot < s1; ++slot) {
+      const int f = static_cast<int>(perm_apply(P, static_cast<uint32_t>(slot)));
+      const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(slot) : static_cast<uint32_t>(f);
+      Cand<CM> c;
+      dense_feature<KIND, CM>(d, nd, rows_in, f, tkey, hw, c);
+      if (better(c, best)) best = c;
+    }
+    if (lane == 0) out[it] = best;
+  }
+}
+
+// One warp per larger node: exact argmax over the node's item candidates,
+// commit, then a stable partition (left rows in order from the front, right
+// rows in order from the back, reversed) with 8 gathers per lane in flight.
+template <int KIND, int CM>
+__global__ void __launch_bounds__(256) k_finalize(Dev d, int level) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t* rows_in = d.rows[level & 1];
+  uint32_t* rows_out = d.rows[(level & 1) ^ 1];
+  const uint32_t nbig = d.work[level];
+  const int G = (d.mtry + kItemsPerNode - 1) / kItemsPerNode;
+  const int ipn = (d.mtry + G - 1) / G;
+  const Cand<CM>* cand = reinterpret_cast<const Cand<CM>*>(d.cand);
+  unsigned long long bytes = 0;
+  for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
+    const uint32_t k = d.big[rank];
+    NodeInfo<CM> nd;
+    load_node<KIND, CM>(d, k, level, nd);
+    Cand<CM> mine;
+    mine.valid = false;
+    if (lane < ipn) mine = cand[static_cast<uint64_t>(rank) * ipn + lane];
+    Cand<CM> best;
+    warp_select<KIND, CM>(mine, best);
+    uint32_t sp = 0;
+    if (lane == 0) sp = commit_split<KIND, CM>(d, k, best, nd);
+    sp = __shfl_sync(kFull, sp, 0);
+    bytes += static_cast<unsigned long long>(nd.len) * (d.mtry + 4ull + (KIND ? 8ull : 0ull));
+    if (sp == kLeaf) continue;
+    const uint8_t* col = d.colptr[sp >> 8];
+    const uint32_t thr = sp & 255u;
+    uint32_t lbase = 0, rbase = 0;
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t r0 = 0; r0 < nd.len; r0 += 256) {
+      uint32_t e[8], b[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t r = r0 + q * 32 + lane;
+        e[q] = r < nd.len ? rows_in[nd.base + r] : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t r = r0 + q * 32 + lane;
+        b[q] = r < nd.len ? col[e[q] >> 8] : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const bool v = r0 + q * 32 + lane < nd.len;
+        const bool gl = v && b[q] <= thr, gr = v && !gl;
+        const unsigned bl = __ballot_sync(kFull, gl), br = __ballot_sync(kFull, gr);
+        if (gl) rows_out[nd.base + lbase + __popc(bl & lt)] = e[q];
+        if (gr) rows_out[nd.base + nd.len - 1u - (rbase + __popc(br & lt))] = e[q];
+        lbase += __popc(bl);
+        rbase += __popc(br);
+      }
+    }
+    if (lane == 0) d.nd_lrows[k] = lbase;
+    bytes += static_cast<unsigned long long>(nd.len) * 5ull;
+  }
+  if (lane == 0 && bytes) atomicAdd(&d.counters[0], bytes);
+}
+
+template <int KIND, int CM>
+void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_t smem, cudaStream_t st) {
+  k_split_small<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+  k_items<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
+  k_finalize<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+}
+
+}  // namespace
+
+int split_variant(int kind, int C) {
+  if (kind != 0) return 3;
+  return C <= 2 ? 0 : (C <= 4 ? 1 : 2);
+}
+
+size_t cand_bytes(int variant) {
+  switch (variant) {
+    case 0: return sizeof(Cand<2>);
+    case 1: return sizeof(Cand<4>);
+    case 2: return sizeof(Cand<8>);
+    default: return sizeof(Cand<1>);
+  }
+}
+
+const void* split_big_ptr(int variant) {
+  switch (variant) {
+    case 0: return reinterpret_cast<const void*>(&k_items<0, 2>);
+    case 1: return reinterpret_cast<const void*>(&k_items<0, 4>);
+    case 2: return reinterpret_cast<const void*>(&k_items<0, 8>);
+    default: return reinterpret_cast<const void*>(&k_items<1, 1>);
+  }
+}
+
+void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st) {
+  switch (split_variant(d.kind, d.C)) {
+    case 0: launch_level<0, 2>(d, level, grid_small, grid_big, smem, st); break;
+    case 1: launch_level<0, 4>(d, level, grid_small, grid_big, smem, st); break;
+    case 2: launch_level<0, 8>(d, level, grid_small, grid_big, smem, st); break;
+    default: launch_level<1, 1>(d, level, grid_small, grid_big, smem, st); break;
+  }
+}
+
+}  // namespace bgb

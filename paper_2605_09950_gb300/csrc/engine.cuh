@@ -76,9 +76,15 @@ void launch_children(const Dev& d, int level, cudaStream_t st);
 void launch_treeimp(const Dev& d, int grid, cudaStream_t st);
 void launch_permut(const Dev& d, int grid, cudaStream_t st);
 void launch_stats_decide(const Dev& d, cudaStream_t st);
-// dynamic shared memory of k_split: one histogram per warp, 16-byte aligned
+// Warp-private histogram layout.  A lane scans 8 consecutive bins, so one
+// padding slot follows every 8 bins: lane l's block then starts at a bank
+// offset coprime with 32 and the scan reads are free of bank conflicts.
+//   classification: count(b, k) at word b*C + k + b/8
+//   regression:     weight(b) at word b + b/8; sum(b) at u64 b + b/8 after the weights
+__host__ __device__ inline int hist_words_n(int B) { return (B + (B >> 3) + 2) & ~1; }
 __host__ __device__ inline size_t split_smem_per_warp(int kind, int C, int B) {
-  const size_t b = kind == 0 ? static_cast<size_t>(B) * C * 4 : static_cast<size_t>(B + 2) * 12;
+  const size_t b = kind == 0 ? (static_cast<size_t>(B) * C + (B >> 3) + 1) * 4
+                             : static_cast<size_t>(hist_words_n(B)) * 4 + static_cast<size_t>(B + (B >> 3) + 1) * 8;
   return (b + 15) & ~static_cast<size_t>(15);
 }
 __host__ __device__ inline size_t split_smem_bytes(int kind, int C, int B) {

@@ -21,6 +21,14 @@
 
 #include "engine.cuh"
 
+// resident CTAs per SM the kernels are compiled for (register budget)
+#ifndef BORUTA_SMALL_MINB
+#define BORUTA_SMALL_MINB 4
+#endif
+#ifndef BORUTA_ITEMS_MINB
+#define BORUTA_ITEMS_MINB 3
+#endif
+
 namespace bgb {
 
 namespace {
@@ -152,9 +160,9 @@ __device__ __forceinline__ void make_reg(Cand<CM>& c, long long SL, long long SP
 
 // Relative window of the float pre-screen.  A float score is within ~2^-21
 // of the exact score, so every candidate whose exact score is the maximum
-// has a float score above (1 - 2^-12) * (best float score); only those are
+// has a float score above (1 - 2^-16) * (best float score); only those are
 // compared exactly.
-__device__ __forceinline__ float screen(float m) { return m - m * 0.000244140625f; }
+__device__ __forceinline__ float screen(float m) { return m - m * 0.0000152587890625f; }
 
 // all lanes: out = best of the lane candidates flagged valid
 template <int KIND, int CM>
@@ -299,7 +307,9 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, bool v, uint32_t b,
       }
     }
   }
-  const bool ok = v && nL < nd.n;
+  // lanes holding the same bin propose the same partition: the lowest one speaks
+  const unsigned same = __match_any_sync(kFull, v ? b : 0xFFFFFFFFu);
+  const bool ok = v && nL < nd.n && (__ffs(same) - 1) == (threadIdx.x & 31);
   float sf = -1.0f;
   if (ok) sf = KIND == 1 ? score_reg_f(SL, nd.SP, nL, nd.n) : score_class_f<CM>(cl, nd.cp, C, nL, nd.n);
   const float mx = warp_max_f(sf);
@@ -320,7 +330,7 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, bool v, uint32_t b,
 }
 
 template <int KIND, int CM>
-__global__ void __launch_bounds__(256) k_split_small(Dev d, int level) {
+__global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, int level) {
   const int lane = threadIdx.x & 31;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -402,11 +412,11 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
   const uint8_t* col = d.colptr[feat];
   constexpr int kBatch = 8;
   uint32_t* hn = hw;
-  unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + ((B + 1) & ~1));
+  unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + hist_words_n(B));
   if (KIND == 0) {
-    for (int i = lane; i < B * C; i += 32) hw[i] = 0u;
+    for (int i = lane; i < B * C + (B >> 3) + 1; i += 32) hw[i] = 0u;
   } else {
-    for (int i = lane; i < B; i += 32) {
+    for (int i = lane; i < B + (B >> 3) + 1; i += 32) {
       hn[i] = 0u;
       hs[i] = 0ull;
     }
@@ -428,7 +438,7 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
     if (KIND == 0) {
 #pragma unroll
       for (int q = 0; q < kBatch; ++q)
-        if (r0 + q * 32 + lane < nd.len) atomicAdd(&hw[b[q] * C + ent_y(e[q])], ent_w<0>(e[q]));
+        if (r0 + q * 32 + lane < nd.len) atomicAdd(&hw[b[q] * C + ent_y(e[q]) + (b[q] >> 3)], ent_w<0>(e[q]));
     } else {
       long long yq[kBatch];
 #pragma unroll
@@ -440,8 +450,8 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
       for (int q = 0; q < kBatch; ++q)
         if (r0 + q * 32 + lane < nd.len) {
           const uint32_t w = ent_w<1>(e[q]);
-          atomicAdd(&hn[b[q]], w);
-          atomicAdd(&hs[b[q]], static_cast<unsigned long long>(static_cast<long long>(w) * yq[q]));
+          atomicAdd(&hn[b[q] + (b[q] >> 3)], w);
+          atomicAdd(&hs[b[q] + (b[q] >> 3)], static_cast<unsigned long long>(static_cast<long long>(w) * yq[q]));
         }
     }
   }
@@ -461,7 +471,7 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
       if (bb < B) {
 #pragma unroll
         for (int k = 0; k < CM; ++k)
-          if (k < C) pre[k] += hw[bb * C + k];
+          if (k < C) pre[k] += hw[bb * C + k + (bb >> 3)];
       }
     }
 #pragma unroll
@@ -474,14 +484,18 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
       sf[q] = -1.0f;
       const int bb = b0 + q;
       if (q < bpl && bb < B - 1) {
-        uint32_t nL = 0;
+        uint32_t nL = 0, wb = 0;
 #pragma unroll
         for (int k = 0; k < CM; ++k)
           if (k < C) {
-            cum[k] += hw[bb * C + k];
+            const uint32_t h = hw[bb * C + k + (bb >> 3)];
+            cum[k] += h;
+            wb += h;
             nL += cum[k];
           }
-        if (nL > 0u && nL < nd.n) {
+        // an empty bin repeats the partition of the nearest non-empty bin
+        // below it, which has the lower bin and wins the tie: skip it
+        if (wb > 0u && nL < nd.n) {
           sf[q] = score_class_f<CM>(cum, nd.cp, C, nL, nd.n);
           lmax = fmaxf(lmax, sf[q]);
         }
@@ -501,7 +515,7 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
 #pragma unroll
         for (int k = 0; k < CM; ++k)
           if (k < C) {
-            cum[k] += hw[bb * C + k];
+            cum[k] += hw[bb * C + k + (bb >> 3)];
             nL += cum[k];
           }
         if (sf[q] >= 0.0f && sf[q] >= thr) {
@@ -520,8 +534,8 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
     for (int q = 0; q < bpl; ++q) {
       const int bb = b0 + q;
       if (bb < B) {
-        tn += hn[bb];
-        ts += static_cast<long long>(hs[bb]);
+        tn += hn[bb + (bb >> 3)];
+        ts += static_cast<long long>(hs[bb + (bb >> 3)]);
       }
     }
     const uint32_t pn = warp_excl_scan_u32(tn, lane);
@@ -533,9 +547,10 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
       sf[q] = -1.0f;
       const int bb = b0 + q;
       if (q < bpl && bb < B - 1) {
-        cn += hn[bb];
-        cs += static_cast<long long>(hs[bb]);
-        if (cn > 0u && cn < nd.n) {
+        const uint32_t hb = hn[bb + (bb >> 3)];
+        cn += hb;
+        cs += static_cast<long long>(hs[bb + (bb >> 3)]);
+        if (hb > 0u && cn < nd.n) {  // empty bins repeat a lower bin's partition
           sf[q] = score_reg_f(cs, nd.SP, cn, nd.n);
           lmax = fmaxf(lmax, sf[q]);
         }
@@ -551,8 +566,8 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
     for (int q = 0; q < 8; ++q) {
       const int bb = b0 + q;
       if (q < bpl && bb < B - 1) {
-        cn += hn[bb];
-        cs += static_cast<long long>(hs[bb]);
+        cn += hn[bb + (bb >> 3)];
+        cs += static_cast<long long>(hs[bb + (bb >> 3)]);
         if (sf[q] >= 0.0f && sf[q] >= thr) {
           Cand<CM> c;
           make_reg<CM>(c, cs, nd.SP, cn, nd.n);
@@ -572,7 +587,7 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
 // few very large nodes (shallow levels) still occupy the whole GPU.  Each
 // item writes its best candidate; k_finalize reduces them per node.
 template <int KIND, int CM>
-__global__ void __launch_bounds__(kSplitThreads, 2) k_items(Dev d, int level) {
+__global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items(Dev d, int level) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
@@ -611,7 +626,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_items(Dev d, int level) {
 // commit, then a stable partition (left rows in order from the front, right
 // rows in order from the back, reversed) with 8 gathers per lane in flight.
 template <int KIND, int CM>
-__global__ void __launch_bounds__(256) k_finalize(Dev d, int level) {
+__global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize(Dev d, int level) {
   const int lane = threadIdx.x & 31;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;

@@ -189,6 +189,25 @@ int boruta_u256_to_double(const uint64_t* v, double* out, int64_t n, void* strea
 int boruta_binom_tails(const int32_t* t, const int32_t* h, double* p_acc, double* p_rej, int64_t n,
                        void* stream);
 
+/* boruta_binom_tails_noalloc -- the same results as boruta_binom_tails,
+ * without allocating anything.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory (a host
+ * program whose own allocator has reserved the GPU's memory, or a path
+ * where cudaMalloc/cudaFree and the device synchronisation they can imply
+ * are not allowed).  The binomial table lives in a fixed device array of
+ * 258,068 bytes that every GPU which loads the library keeps until the
+ * process exits.
+ *   t, h   [in]  device int32[n]; t must lie in [0, 126] (else BORUTA_EINVAL,
+ *                and the entries with a bad t are written as NaN)
+ *   p_acc, p_rej [out] device double[n], as for boruta_binom_tails
+ *   stream [in]  cudaStream_t (NULL = legacy default stream); the call waits for it
+ * The first call on a device looks up the array's address and fills the
+ * table (with that device current); make that first call before any stream
+ * capture.  All calls share the array: its error word is cleared at the
+ * start of each call, and calls that overlap on the GPU race on it. */
+int boruta_binom_tails_noalloc(const int32_t* t, const int32_t* h, double* p_acc, double* p_rej,
+                               int64_t n, void* stream);
+
 /* Message for the last error on this thread ("" if none). */
 const char* boruta_last_error(void);
 

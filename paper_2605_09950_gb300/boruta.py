@@ -26,7 +26,7 @@ EXPORTS = [
     "boruta_default_opts", "boruta_fit", "boruta_session_create", "boruta_session_step",
     "boruta_session_read", "boruta_session_write", "boruta_session_dump",
     "boruta_session_kernel_stats", "boruta_session_destroy", "boruta_philox", "boruta_perm",
-    "boruta_u256_to_double", "boruta_binom_tails", "boruta_last_error",
+    "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_last_error",
 ]
 
 
@@ -84,6 +84,7 @@ def lib():
                                   i64, vp]
         L.boruta_u256_to_double.argtypes = [vp, vp, i64, vp]
         L.boruta_binom_tails.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.boruta_binom_tails_noalloc.argtypes = [vp, vp, vp, vp, i64, vp]
         L.boruta_last_error.restype = ct.c_char_p
         for name in EXPORTS:
             if name not in ("boruta_default_opts", "boruta_session_destroy", "boruta_last_error"):
@@ -231,3 +232,11 @@ def boruta_binom_tails(t, h):
     _check(lib().boruta_binom_tails(t.data_ptr(), h.data_ptr(), pa.data_ptr(), pr.data_ptr(), t.numel(),
                                     _stream()))
     return pa, pr
+
+
+def boruta_binom_tails_noalloc(t, h, p_acc, p_rej):
+    """Same as boruta_binom_tails, writing into caller-provided tensors and
+    allocating nothing on the device (fixed table inside the library)."""
+    _check(lib().boruta_binom_tails_noalloc(t.data_ptr(), h.data_ptr(), p_acc.data_ptr(), p_rej.data_ptr(),
+                                            t.numel(), _stream()))
+    return p_acc, p_rej

@@ -48,6 +48,9 @@ int64_t isqrt(int64_t v) {
 
 }  // namespace
 
+// error reporting for noalloc.cu (same thread-local message as every entry point)
+int boruta_noalloc_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct boruta_session {
   Dev d{};
   cudaStream_t st = nullptr;

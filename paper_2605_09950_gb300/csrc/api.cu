@@ -63,10 +63,8 @@ struct boruta_session {
   uint32_t* status_h = nullptr;
   int8_t* state_pin = nullptr;
   int32_t* live_pin = nullptr;
-  const uint8_t** colptr_pin = nullptr;
   // device per-iteration arrays
   int32_t* live_d = nullptr;
-  const uint8_t** colptr_d = nullptr;
   uint8_t* X_owned = nullptr;
   void* y_owned = nullptr;
   // launch geometry
@@ -101,7 +99,6 @@ struct boruta_session {
     if (status_h) cudaFreeHost(status_h);
     if (state_pin) cudaFreeHost(state_pin);
     if (live_pin) cudaFreeHost(live_pin);
-    if (colptr_pin) cudaFreeHost(colptr_pin);
   }
 };
 
@@ -194,10 +191,9 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   const int Cmax = kMaxClasses;
 
   if ((rc = s->alloc(&s->live_d, p))) return rc;
-  if ((rc = s->alloc(&s->colptr_d, p_aug_max))) return rc;
   d.live = s->live_d;
-  d.colptr = s->colptr_d;
-  if ((rc = s->alloc(&d.Xsha, static_cast<size_t>(n_sha_max) * d.ldN))) return rc;
+  (void)n_sha_max;
+  if ((rc = s->alloc(&d.Xaug, static_cast<size_t>(p_aug_max) * d.ldN))) return rc;
   const size_t MN = static_cast<size_t>(n_trees) * N;
   if ((rc = s->alloc(&d.bootcnt, MN))) return rc;
   if ((rc = s->alloc(&d.rows[0], MN))) return rc;
@@ -223,7 +219,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   if ((rc = s->alloc(&d.lvl_cnt, max_depth + 2))) return rc;
   if ((rc = s->alloc(&d.work, max_depth + 2))) return rc;
   if ((rc = s->alloc(&d.chunk, kScanBlocks))) return rc;
-  if ((rc = s->alloc(&d.acc, static_cast<size_t>(n_trees) * p_aug_max * kFixLimbs))) return rc;
+  if ((rc = s->alloc(&d.acc, static_cast<size_t>(n_trees) * p_aug_max * kCsaLimbs))) return rc;
   if ((rc = s->alloc(&d.imp, static_cast<size_t>(n_trees) * p_aug_max))) return rc;
   if ((rc = s->alloc(&d.s, p_aug_max))) return rc;
   if ((rc = s->alloc(&d.state, p))) return rc;
@@ -239,7 +235,6 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   CK(cudaHostAlloc(&s->status_h, 4 * sizeof(uint32_t), cudaHostAllocDefault));
   CK(cudaHostAlloc(&s->state_pin, p, cudaHostAllocDefault));
   CK(cudaHostAlloc(&s->live_pin, p * sizeof(int32_t), cudaHostAllocDefault));
-  CK(cudaHostAlloc(reinterpret_cast<void**>(&s->colptr_pin), p_aug_max * sizeof(void*), cudaHostAllocDefault));
 
   // binomial coefficients C(t, k), t, k <= 126, by Pascal's rule (exact)
   std::vector<u128> tri(127 * 127, 0);
@@ -292,6 +287,20 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   uint8_t* cand = nullptr;
   if ((rc = s->alloc(&cand, big_cap * kItemsPerNode * cand_bytes(split_variant(d.kind, d.C))))) return rc;
   d.cand = cand;
+  // feature-band plan buffers: one item per (larger node, draw slot)
+  {
+    const int64_t mtry_max = mtry > 0 ? std::min<int64_t>(mtry, p_aug_max)
+                                      : std::max<int64_t>(1, reg ? p_aug_max / 3 : isqrt(p_aug_max));
+    uint64_t cap_items = static_cast<uint64_t>(big_cap) * static_cast<uint64_t>(mtry_max);
+    if (cap_items > kMaxItems) cap_items = kMaxItems;
+    d.item_cap = cap_items;
+    if ((rc = s->alloc(&d.items_u, cap_items))) return rc;
+    if ((rc = s->alloc(&d.items_s, cap_items))) return rc;
+    uint8_t* fb = nullptr;
+    if ((rc = s->alloc(&fb, cap_items * packed_bytes(split_variant(d.kind, d.C))))) return rc;
+    d.fbest = fb;
+    if ((rc = s->alloc(&d.band_cnt, kMaxBands))) return rc;
+  }
   (void)Cmax;
   CK(cudaMemsetAsync(d.status, 0, 4 * sizeof(uint32_t), s->st));
 
@@ -300,10 +309,13 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev));
   s->split_smem = split_smem_bytes(d.kind, d.C, d.B);
-  const void* big = split_big_ptr(split_variant(d.kind, d.C));
-  CK(cudaFuncSetAttribute(big, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(s->split_smem)));
+  const void* kptr[4];
+  int nk = 0;
+  split_kernel_ptrs(split_variant(d.kind, d.C), kptr, &nk);
+  for (int i = 0; i < nk; ++i)
+    CK(cudaFuncSetAttribute(kptr[i], cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(s->split_smem)));
   int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big, kSplitThreads, s->split_smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kptr[1], kSplitThreads, s->split_smem));
   if (per_sm < 1) return fail(BORUTA_EINVAL, "split kernel does not fit on an SM");
   s->split_grid = per_sm * s->sms;
   s->small_grid = 8 * s->sms;
@@ -351,8 +363,6 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
     if (s->state_h[j] >= 0) s->live_pin[p_live++] = static_cast<int32_t>(j);
   const int64_t n_sha = shadow_count(p_live);
   const int64_t p_aug = p_live + n_sha;
-  for (int32_t a = 0; a < p_live; ++a) s->colptr_pin[a] = d.X + static_cast<int64_t>(s->live_pin[a]) * d.ld;
-  for (int64_t c = 0; c < n_sha; ++c) s->colptr_pin[p_live + c] = d.Xsha + c * d.ldN;
   d.t = t;
   d.p_live = p_live;
   d.n_sha = static_cast<int32_t>(n_sha);
@@ -360,15 +370,25 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   int64_t m = s->mtry_opt > 0 ? std::min<int64_t>(s->mtry_opt, p_aug)
                               : (d.kind ? p_aug / 3 : isqrt(p_aug));
   d.mtry = static_cast<int32_t>(std::max<int64_t>(m, 1));
+  // feature bands: ~kBandBytes of columns each, at most kMaxBands; the packed
+  // item holds a 14-bit slot and a 22-bit feature
+  d.band_w = 0;
+  d.nbands = 0;
+  if (d.item_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
+    int64_t w = std::max<int64_t>(1, kBandBytes / d.ldN);
+    w = std::max<int64_t>(w, (p_aug + kMaxBands - 1) / kMaxBands);
+    d.band_w = static_cast<int32_t>(w);
+    d.nbands = static_cast<int32_t>((p_aug + w - 1) / w);
+  }
 
   CK(cudaMemcpyAsync(s->live_d, s->live_pin, p_live * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(s->colptr_d, s->colptr_pin, p_aug * sizeof(void*), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d.bootcnt, 0, static_cast<size_t>(d.M) * d.N * sizeof(uint32_t), st));
-  CK(cudaMemsetAsync(d.acc, 0, static_cast<size_t>(d.M) * p_aug * kFixLimbs * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(d.acc, 0, static_cast<size_t>(d.M) * p_aug * kCsaLimbs * sizeof(long long), st));
   CK(cudaMemsetAsync(d.work, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.lvl_cnt, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.counters, 0, sizeof(unsigned long long), st));
 
+  launch_gather_live(d, st);
   launch_shadow(d, st);
   launch_bootstrap(d, s->tree_grid, st);
   for (int level = 0; level < d.D; ++level) {
@@ -483,7 +503,8 @@ int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacit
       if (bytes) *bytes = need;
       if (!host) return 0;
       if (capacity < need) return fail(BORUTA_EINVAL, "capacity too small");
-      CK(cudaMemcpy2DAsync(host, d.N, d.Xsha, d.ldN, d.N, d.n_sha, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpy2DAsync(host, d.N, d.Xaug + static_cast<int64_t>(d.p_live) * d.ldN, d.ldN, d.N, d.n_sha,
+                           cudaMemcpyDeviceToHost, s->st));
       CK(cudaStreamSynchronize(s->st));
       return 0;
     }

@@ -322,6 +322,65 @@ __device__ inline float fix_to_float(const uint64_t acc[kFixLimbs]) {
   return neg ? -r : r;
 }
 
+// ---------------------------------------------------------------- carry-save accumulation
+// The same exact value in a form that concurrent adders update without
+// reading back: 12 signed 64-bit limbs, limb i weighing 2^(32 i - 192); a
+// term adds (or subtracts) its 32-bit chunks to at most three limbs, so no
+// carry moves between limbs while terms arrive (a limb absorbs 2^31 terms
+// without overflow).  Carries are propagated once, when the sum is read.
+constexpr int kCsaLimbs = 12;
+
+// false (nothing added) for magnitudes >= 2^190 or non-finite terms
+__device__ inline bool csa_add(long long* acc, double x) {
+  if (x == 0.0) return true;
+  const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(x));
+  const bool neg = bits >> 63;
+  const int eraw = static_cast<int>((bits >> 52) & 0x7FF);
+  if (eraw == 0x7FF) return false;
+  uint64_t m = bits & ((1ull << 52) - 1ull);
+  int e;
+  if (eraw) {
+    m |= 1ull << 52;
+    e = eraw - 1075;
+  } else {
+    e = -1074;
+  }
+  int pos = e + kFixShift;
+  if (pos < 0) {
+    m = (-pos >= 64) ? 0ull : (m >> (-pos));
+    pos = 0;
+  }
+  if (m == 0) return true;
+  if (pos + 53 > 32 * kCsaLimbs - 2) return false;
+  const int li = pos >> 5, off = pos & 31;
+  const u128 v = static_cast<u128>(m) << off;
+  const uint32_t c[3] = {static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32),
+                         static_cast<uint32_t>(v >> 64)};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (c[q]) {
+      const long long s = neg ? -static_cast<long long>(c[q]) : static_cast<long long>(c[q]);
+      atomicAdd(reinterpret_cast<unsigned long long*>(acc + li + q), static_cast<unsigned long long>(s));
+    }
+  }
+  return true;
+}
+
+// carry-save limbs -> 384-bit two's complement (kFixLimbs u64 limbs)
+__device__ inline void csa_to_fix(const long long* acc, uint64_t out[kFixLimbs]) {
+  __int128 carry = 0;
+  uint32_t w[kCsaLimbs];
+#pragma unroll
+  for (int i = 0; i < kCsaLimbs; ++i) {
+    const __int128 s = carry + static_cast<__int128>(acc[i]);
+    w[i] = static_cast<uint32_t>(static_cast<unsigned __int128>(s) & 0xFFFFFFFFu);
+    carry = s >> 32;  // arithmetic: keeps the sign
+  }
+#pragma unroll
+  for (int i = 0; i < kFixLimbs; ++i)
+    out[i] = static_cast<uint64_t>(w[2 * i]) | (static_cast<uint64_t>(w[2 * i + 1]) << 32);
+}
+
 // ---------------------------------------------------------------- warp helpers
 __device__ __forceinline__ uint32_t warp_excl_scan_u32(uint32_t v, int lane) {
   uint32_t x = v;

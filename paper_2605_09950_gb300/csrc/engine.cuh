@@ -24,9 +24,8 @@ struct Dev {
   // ---- iteration
   int32_t t, p_live, n_sha, p_aug, mtry;
   const int32_t* live;           // [p_live]
-  const uint8_t* const* colptr;  // [p_aug] augmented column pointers
   // ---- buffers
-  uint8_t* Xsha;                 // [n_sha][ldN]
+  uint8_t* Xaug;                 // [p_aug][ldN]: live original columns, then the shadows
   uint32_t* bootcnt;             // [M][N] bootstrap draw counts
   uint32_t* rows[2];             // [M][N] node-ordered row entries (row << 8 | weight)
   uint32_t* oob;                 // [M][N] out-of-bag rows, ascending
@@ -45,9 +44,15 @@ struct Dev {
   uint32_t* work;                // [D + 2] per level: number of nodes in `big`
   uint32_t* chunk;               // [kScanBlocks] per-block split counts
   uint32_t* big;                 // [big_cap] this level's active nodes with > 32 rows
-  void* cand;                    // [big_cap * kItemsPerNode] best candidate per work item
+  void* cand;                    // [big_cap * kItemsPerNode] best candidate per grouped item
+  uint64_t* items_u;             // [item_cap] (node rank, slot, feature) per item, node order
+  uint64_t* items_s;             // [item_cap] the same, sorted by feature band
+  void* fbest;                   // [item_cap] packed best candidate per (node rank, slot)
+  uint32_t* band_cnt;            // [kMaxBands] band sizes, then cursors
+  uint64_t item_cap;
+  int32_t band_w, nbands;        // columns per band (0: grouped path only), bands
   // ---- importance and Boruta state
-  unsigned long long* acc;       // [M][p_aug][6] exact per-tree accumulators
+  long long* acc;                // [M][p_aug][kCsaLimbs] exact per-tree accumulators (carry-save)
   double* imp;                   // [M][p_aug]
   double* s;                     // [p_aug]
   const u128* pascal;            // [127][127] binomial coefficients C(t, k)
@@ -62,6 +67,9 @@ struct Dev {
 constexpr int kScanBlocks = 512;
 constexpr int kSplitThreads = 256;
 constexpr int kItemsPerNode = 16;  // work items (groups of draw slots) per larger node
+constexpr int kMaxBands = 256;     // feature bands of the band-sorted path
+constexpr int64_t kBandBytes = 24ll << 20;  // column bytes per band (kept in L2 while in use)
+constexpr uint64_t kMaxItems = 64ull << 20;  // plan buffer capacity (items)
 
 // launchers (kernels.cu)
 void launch_validate(const Dev& d, cudaStream_t st);
@@ -70,8 +78,10 @@ void launch_bootstrap(const Dev& d, int grid, cudaStream_t st);
 // split.cu: k_split_small (nodes <= 32 rows) then k_split_big on one level
 void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st);
 int split_variant(int kind, int C);
-const void* split_big_ptr(int variant);
+void split_kernel_ptrs(int variant, const void** ptrs, int* n);  // kernels taking dynamic shared memory
 size_t cand_bytes(int variant);
+size_t packed_bytes(int variant);
+void launch_gather_live(const Dev& d, cudaStream_t st);
 void launch_children(const Dev& d, int level, cudaStream_t st);
 void launch_treeimp(const Dev& d, int grid, cudaStream_t st);
 void launch_permut(const Dev& d, int grid, cudaStream_t st);

@@ -102,7 +102,31 @@ void launch_validate(const Dev& d, cudaStream_t st) {
 }
 
 // ============================================================ Alg. 1: shadow features
-// Xsha[c][i] = X[sigma_c(i)][live[c mod p_live]]; 16 rows per thread, one
+// X_cur into the augmented matrix: Xaug[a] = X[live[a]] (16-byte copies when
+// the caller's columns allow it).  The augmented columns then sit at a fixed
+// stride, so every kernel addresses column f as Xaug + f * ldN.
+__global__ void k_gather_live(Dev d, int vec) {
+  const int a = blockIdx.y;
+  const uint8_t* src = d.X + static_cast<int64_t>(d.live[a]) * d.ld;
+  uint8_t* dst = d.Xaug + static_cast<int64_t>(a) * d.ldN;
+  if (vec) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* t = reinterpret_cast<uint4*>(dst);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ldN / 16; i += gridDim.x * blockDim.x) t[i] = s[i];
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) dst[i] = src[i];
+  }
+}
+
+void launch_gather_live(const Dev& d, cudaStream_t st) {
+  // 16-byte path: aligned base, ld a multiple of 16 and at least ldN bytes per column
+  const int vec = (reinterpret_cast<uintptr_t>(d.X) % 16 == 0) && (d.ld % 16 == 0) && (d.ld >= d.ldN);
+  int bx = ((vec ? d.ldN / 16 : d.N) + 255) / 256;
+  if (bx > 16) bx = 16;
+  k_gather_live<<<dim3(bx, d.p_live), 256, 0, st>>>(d, vec);
+}
+
+// Xaug[p_live + c][i] = X[sigma_c(i)][live[c mod p_live]]; 16 rows per thread, one
 // 16-byte store.  The source column is read through L2 (random gather).
 __global__ void k_shadow(Dev d) {
   const int c = blockIdx.y;
@@ -113,7 +137,7 @@ __global__ void k_shadow(Dev d) {
   __syncthreads();
   const Perm P = sp;
   const uint8_t* src = d.X + static_cast<int64_t>(d.live[c % d.p_live]) * d.ld;
-  uint8_t* dst = d.Xsha + static_cast<int64_t>(c) * d.ldN;
+  uint8_t* dst = d.Xaug + static_cast<int64_t>(d.p_live + c) * d.ldN;
   for (int base = (blockIdx.x * blockDim.x + threadIdx.x) * 16; base < d.N;
        base += gridDim.x * blockDim.x * 16) {
     uint32_t v[4] = {0u, 0u, 0u, 0u};
@@ -336,10 +360,8 @@ __global__ void k_treeimp_norm(Dev d) {
     for (int i = 0; i < kFixLimbs; ++i) a[i] = 0;
     bool bad = false;
     for (int j = threadIdx.x; j < d.p_aug; j += blockDim.x) {
-      const unsigned long long* src = d.acc + (static_cast<int64_t>(tau) * d.p_aug + j) * kFixLimbs;
       uint64_t g[kFixLimbs];
-#pragma unroll
-      for (int i = 0; i < kFixLimbs; ++i) g[i] = src[i];
+      csa_to_fix(d.acc + (static_cast<int64_t>(tau) * d.p_aug + j) * kCsaLimbs, g);
       const double gj = d.precision == 0 ? fix_to_double(g) : static_cast<double>(fix_to_float(g));
       d.imp[static_cast<int64_t>(tau) * d.p_aug + j] = gj;
       uint64_t v[kFixLimbs];
@@ -395,7 +417,7 @@ __device__ __forceinline__ uint32_t leaf_of(const Dev& d, uint32_t k, uint32_t r
     const uint32_t sp = d.nd_split[k];
     if (sp == kLeaf) return k;
     const int g = static_cast<int>(sp >> 8);
-    const uint8_t x = (g == f) ? xf : d.colptr[g][row];
+    const uint8_t x = (g == f) ? xf : d.Xaug[static_cast<int64_t>(g) * d.ldN + row];
     k = d.nd_child[k] + (x > (sp & 255u) ? 1u : 0u);
   }
   return k;
@@ -424,15 +446,14 @@ __device__ double loss64(const Dev& d, uint32_t q, uint32_t q2) {
 __device__ __forceinline__ float kl_phi(float r) {
   const float dl = r - 1.0f;
   if (fabsf(dl) < 0.25f) {
-    // sum_{n>=2} (-1)^n dl^n / (n (n-1))
-    float s = 0.0f, pw = dl * dl;
+    // dl^2 * sum_{n=2..14} (-1)^n dl^(n-2) / (n (n-1)), by Horner
+    constexpr float c[13] = {1.0f / 2,   -1.0f / 6,   1.0f / 12,   -1.0f / 20,  1.0f / 30,
+                             -1.0f / 42, 1.0f / 56,   -1.0f / 72,  1.0f / 90,   -1.0f / 110,
+                             1.0f / 132, -1.0f / 156, 1.0f / 182};
+    float s = c[12];
 #pragma unroll
-    for (int n = 2; n <= 14; ++n) {
-      const float term = pw / static_cast<float>(n * (n - 1));
-      s += (n & 1) ? -term : term;
-      pw *= dl;
-    }
-    return s;
+    for (int m = 11; m >= 0; --m) s = s * dl + c[m];
+    return s * (dl * dl);
   }
   return r * logf(r) - dl;
 }
@@ -478,32 +499,42 @@ __global__ void k_permut(Dev d) {
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < noob; r += gridDim.x * blockDim.x) {
       const uint32_t i = oob[r];
       const uint32_t pi = perm_apply(P, i);
-      uint32_t path[kMaxDepth];
+      // the row's path: node, split word, and the row's own bin at each node
+      uint32_t path[kMaxDepth], pw[kMaxDepth];
+      uint8_t px[kMaxDepth];
       int depth = 0;
       uint32_t k = static_cast<uint32_t>(tau);
       while (depth < kMaxDepth) {
         const uint32_t s = d.nd_split[k];
         if (s == kLeaf) break;
-        path[depth++] = k;
-        const uint8_t x = d.colptr[s >> 8][i];
+        const uint8_t x = d.Xaug[static_cast<int64_t>(s >> 8) * d.ldN + i];
+        path[depth] = k;
+        pw[depth] = s;
+        px[depth] = x;
+        ++depth;
         k = d.nd_child[k] + (x > (s & 255u) ? 1u : 0u);
       }
       const uint32_t q = k;
       for (int a = 0; a < depth; ++a) {
-        const int f = static_cast<int>(d.nd_split[path[a]] >> 8);
+        const uint32_t f = pw[a] >> 8;
         bool seen = false;
-        for (int b = 0; b < a; ++b) seen |= static_cast<int>(d.nd_split[path[b]] >> 8) == f;
+        for (int b = 0; b < a; ++b) seen |= (pw[b] >> 8) == f;
         if (seen) continue;
-        const uint8_t xp = d.colptr[f][pi];
-        const uint32_t q2 = leaf_of(d, path[a], i, f, xp);
+        const uint8_t xp = d.Xaug[static_cast<int64_t>(f) * d.ldN + pi];
+        if (xp == px[a]) continue;  // same value: same leaf
+        // The swapped row follows the recorded path until the first node on
+        // it that tests f and sends xp the other way; if there is none it
+        // reaches the same leaf (loss exactly 0).
+        int b = a;
+        for (; b < depth; ++b)
+          if ((pw[b] >> 8) == f && ((xp > (pw[b] & 255u)) != (px[b] > (pw[b] & 255u)))) break;
+        if (b == depth) continue;
+        const uint32_t start = d.nd_child[path[b]] + (xp > (pw[b] & 255u) ? 1u : 0u);
+        const uint32_t q2 = leaf_of(d, start, i, static_cast<int>(f), xp);
         if (q2 == q) continue;
         const double L = d.precision == 0 ? loss64(d, q, q2) : static_cast<double>(loss32(d, q, q2));
-        uint64_t v[kFixLimbs];
-        if (!fix_from_double(L, v)) {
+        if (!csa_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + f) * kCsaLimbs, L))
           atomicOr(&d.status[0], kErrAcc);
-          continue;
-        }
-        fix_atomic_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + f) * kFixLimbs, v);
       }
     }
   }
@@ -516,8 +547,7 @@ __global__ void k_permut_final(Dev d) {
     const int tau = static_cast<int>(g / d.p_aug);
     const uint32_t n = d.oob_cnt[tau];
     uint64_t a[kFixLimbs];
-#pragma unroll
-    for (int i = 0; i < kFixLimbs; ++i) a[i] = d.acc[g * kFixLimbs + i];
+    csa_to_fix(d.acc + g * kCsaLimbs, a);
     double v = 0.0;
     if (n > 0) {
       if (d.precision == 0)

@@ -2,16 +2,26 @@
 // sample, histograms, exact best-split scan, impurity decrease into the
 // TreeImp accumulators (Alg. 2) and the stable row partition.
 //
-// Two kernels share a level:
-//   k_split_small  one warp per node with at most 32 distinct rows: one row
-//                  per lane, candidate thresholds at the bins present, left
-//                  counts from a warp-wide compare loop (no histogram);
-//   k_items        larger nodes, one warp per (node, group of draw slots):
-//                  a warp-private shared-memory histogram per feature from
-//                  batched gathers, a warp prefix scan over the bins, the
-//                  best candidate of the group;
-//   k_finalize     one warp per larger node: exact argmax over its groups,
-//                  the split record, and the stable row partition.
+// Kernels of a level:
+//   k_split_small   one warp per node with at most 32 distinct rows: one row
+//                   per lane, candidate thresholds at the bins present, left
+//                   counts from a warp-wide compare loop (no histogram); it
+//                   also lists the level's larger active nodes.
+//   larger nodes, feature-band path (default):
+//     k_plan_gen / k_plan_scan / k_plan_scatter  one work item per (node,
+//                   draw slot), counting-sorted by the band of columns its
+//                   feature lies in, so that the columns being gathered at
+//                   any moment fit in L2;
+//     k_items_band  one warp per item: warp-private shared-memory histogram
+//                   from batched gathers, warp prefix scan over the bins,
+//                   the feature's exact best candidate, kept as the integers
+//                   that define it (feature, bin, left counts);
+//     k_finalize_band  one warp per node: exact argmax over its features'
+//                   candidates (rebuilt from those integers), split record
+//                   and partition.
+//   larger nodes, grouped path (when a level has more items than the plan
+//   buffers hold): k_items (one warp per group of draw slots, exact) and
+//   k_finalize (exact argmax over groups, record, partition).
 // Candidate (f, b): rows with bin <= b go left.  Score num/den =
 // (A_L n_R + A_R n_L) / (n_L n_R) with A = sum_k c_k^2 (Gini) or S^2
 // (variance); scores are compared exactly (256-bit cross products) after a
@@ -39,6 +49,10 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+__device__ __forceinline__ const uint8_t* column(const Dev& d, uint32_t f) {
+  return d.Xaug + static_cast<int64_t>(f) * d.ldN;
 }
 
 // Row entries: row << 8 | low byte.  Classification: low byte = y << 5 | w
@@ -158,10 +172,10 @@ __device__ __forceinline__ void make_reg(Cand<CM>& c, long long SL, long long SP
   c.valid = true;
 }
 
-// Relative window of the float pre-screen.  A float score is within ~2^-21
-// of the exact score, so every candidate whose exact score is the maximum
-// has a float score above (1 - 2^-16) * (best float score); only those are
-// compared exactly.
+// Relative window of the float pre-screen.  A float score is within 2^-21 of
+// the exact score, so every candidate whose exact score is the maximum has a
+// float score above (1 - 2^-16) * (best float score); only those are compared
+// exactly.
 __device__ __forceinline__ float screen(float m) { return m - m * 0.0000152587890625f; }
 
 // all lanes: out = best of the lane candidates flagged valid
@@ -249,11 +263,8 @@ __device__ uint32_t commit_split(const Dev& d, uint32_t k, const Cand<CM>& b, co
         if (c < d.C) d.nd_lcnt[static_cast<int64_t>(k) * d.C + c] = b.cL[c];
     }
     if (!d.permut) {  // Alg. 2: this node's gain x samples, summed exactly per (tree, feature)
-      uint64_t v[kFixLimbs];
-      if (!fix_from_double(delta, v))
+      if (!csa_add(d.acc + (static_cast<int64_t>(d.nd_tree[k]) * d.p_aug + b.feat) * kCsaLimbs, delta))
         atomicOr(&d.status[0], kErrAcc);
-      else
-        fix_atomic_add(d.acc + (static_cast<int64_t>(d.nd_tree[k]) * d.p_aug + b.feat) * kFixLimbs, v);
     }
   }
   d.nd_split[k] = sp;
@@ -278,6 +289,47 @@ __device__ bool load_node(const Dev& d, uint32_t k, int level, NodeInfo<CM>& nd)
   }
   if (KIND == 1) nd.SP = d.nd_S[k];
   return level < d.D && nd.len >= 2u && !pure;
+}
+
+__device__ __forceinline__ void node_perm(const Dev& d, uint32_t k, Perm& P) {
+  perm_init(P, static_cast<uint32_t>(d.p_aug), d.seed, d.nd_heap[k], unit_word(d.t, d.nd_tree[k]),
+            purpose_word(kPurposeMtry, d.job));
+}
+
+// Stable partition of a node's rows by warp: left rows in order from the
+// front, right rows in order from the back (reversed); 8 gathers per lane
+// in flight.  Returns the number of left rows.
+__device__ uint32_t warp_partition(const Dev& d, int64_t base, uint32_t len, uint32_t sp, const uint32_t* rows_in,
+                                   uint32_t* rows_out) {
+  const int lane = threadIdx.x & 31;
+  const uint8_t* col = column(d, sp >> 8);
+  const uint32_t thr = sp & 255u;
+  uint32_t lbase = 0, rbase = 0;
+  const uint32_t lt = lanemask_lt();
+  for (uint32_t r0 = 0; r0 < len; r0 += 256) {
+    uint32_t e[8], b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t r = r0 + q * 32 + lane;
+      e[q] = r < len ? rows_in[base + r] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t r = r0 + q * 32 + lane;
+      b[q] = r < len ? col[e[q] >> 8] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool v = r0 + q * 32 + lane < len;
+      const bool gl = v && b[q] <= thr, gr = v && !gl;
+      const unsigned bl = __ballot_sync(kFull, gl), br = __ballot_sync(kFull, gr);
+      if (gl) rows_out[base + lbase + __popc(bl & lt)] = e[q];
+      if (gr) rows_out[base + len - 1u - (rbase + __popc(br & lt))] = e[q];
+      lbase += __popc(bl);
+      rbase += __popc(br);
+    }
+  }
+  return lbase;
 }
 
 // ============================================================ small nodes
@@ -347,13 +399,12 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
       if (lane == 0) d.nd_split[k] = kLeaf;
       continue;
     }
-    if (nd.len > 32u) {  // handled by k_items / k_finalize
+    if (nd.len > 32u) {  // a larger node: listed for the item kernels
       if (lane == 0) d.big[atomicAdd(&d.work[level], 1u)] = k;
       continue;
     }
     Perm P;
-    perm_init(P, static_cast<uint32_t>(d.p_aug), d.seed, d.nd_heap[k], unit_word(d.t, d.nd_tree[k]),
-              purpose_word(kPurposeMtry, d.job));
+    node_perm(d, k, P);
     const bool v = lane < static_cast<int>(nd.len);
     const uint32_t e = v ? rows_in[nd.base + lane] : 0u;
     const uint32_t row = e >> 8, w = v ? ent_w<KIND>(e) : 0u;
@@ -365,18 +416,17 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
       const int ns = min(32, d.mtry - r0);
       const uint32_t myf = lane < ns ? perm_apply(P, static_cast<uint32_t>(r0 + lane)) : 0u;
       for (int j = 0; j < ns; j += 4) {
-        int fq[4];
-        uint32_t bq[4];
+        uint32_t fq[4], bq[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) fq[q] = static_cast<int>(__shfl_sync(kFull, myf, min(j + q, ns - 1)));
+        for (int q = 0; q < 4; ++q) fq[q] = __shfl_sync(kFull, myf, min(j + q, ns - 1));
 #pragma unroll
-        for (int q = 0; q < 4; ++q) bq[q] = (v && j + q < ns) ? d.colptr[fq[q]][row] : 0u;
+        for (int q = 0; q < 4; ++q) bq[q] = (v && j + q < ns) ? column(d, fq[q])[row] : 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (j + q < ns) {
-            const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(r0 + j + q) : static_cast<uint32_t>(fq[q]);
+            const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(r0 + j + q) : fq[q];
             Cand<CM> c;
-            small_feature<KIND, CM>(nd, C, v, bq[q], w, y, yv, fq[q], tkey, c);
+            small_feature<KIND, CM>(nd, C, v, bq[q], w, y, yv, static_cast<int>(fq[q]), tkey, c);
             if (better(c, best)) best = c;
           }
         }
@@ -388,7 +438,7 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
     bytes += static_cast<unsigned long long>(nd.len) * (d.mtry + 4ull + (KIND ? 8ull : 0ull));
     if (sp == kLeaf) continue;
     // stable partition: left rows in order, then right rows in order
-    const uint32_t bs = v ? d.colptr[sp >> 8][row] : 0u;
+    const uint32_t bs = v ? column(d, sp >> 8)[row] : 0u;
     const bool gl = v && bs <= (sp & 255u), gr = v && !gl;
     const unsigned bl = __ballot_sync(kFull, gl), br = __ballot_sync(kFull, gr);
     const uint32_t nl = __popc(bl);
@@ -401,15 +451,14 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
 }
 
 // ============================================================ larger nodes
-// Best split of one feature of a node with > 32 rows, warp-wide, from a
-// warp-private histogram.  Rows are gathered 8 per lane per pass so that 8
-// independent loads per lane are in flight.
-template <int KIND, int CM>
-__device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* rows, int feat, uint32_t tkey,
-                              uint32_t* hw, Cand<CM>& out) {
+// Warp-private histogram of one feature over a node's rows.  Rows are
+// gathered 8 per lane per pass so that 8 independent loads per lane are in
+// flight.
+template <int KIND>
+__device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint32_t* rows, const uint8_t* col,
+                           uint32_t* hw) {
   const int lane = threadIdx.x & 31;
   const int C = d.C, B = d.B;
-  const uint8_t* col = d.colptr[feat];
   constexpr int kBatch = 8;
   uint32_t* hn = hw;
   unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + hist_words_n(B));
@@ -422,33 +471,33 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
     }
   }
   __syncwarp();
-  for (uint32_t r0 = 0; r0 < nd.len; r0 += 32 * kBatch) {
+  for (uint32_t r0 = 0; r0 < len; r0 += 32 * kBatch) {
     uint32_t e[kBatch];
     uint32_t b[kBatch];
 #pragma unroll
     for (int q = 0; q < kBatch; ++q) {
       const uint32_t r = r0 + q * 32 + lane;
-      e[q] = r < nd.len ? rows[nd.base + r] : 0u;
+      e[q] = r < len ? rows[base + r] : 0u;
     }
 #pragma unroll
     for (int q = 0; q < kBatch; ++q) {
       const uint32_t r = r0 + q * 32 + lane;
-      b[q] = r < nd.len ? col[e[q] >> 8] : 0u;
+      b[q] = r < len ? col[e[q] >> 8] : 0u;
     }
     if (KIND == 0) {
 #pragma unroll
       for (int q = 0; q < kBatch; ++q)
-        if (r0 + q * 32 + lane < nd.len) atomicAdd(&hw[b[q] * C + ent_y(e[q]) + (b[q] >> 3)], ent_w<0>(e[q]));
+        if (r0 + q * 32 + lane < len) atomicAdd(&hw[b[q] * C + ent_y(e[q]) + (b[q] >> 3)], ent_w<0>(e[q]));
     } else {
       long long yq[kBatch];
 #pragma unroll
       for (int q = 0; q < kBatch; ++q) {
         const uint32_t r = r0 + q * 32 + lane;
-        yq[q] = r < nd.len ? d.yreg[e[q] >> 8] : 0ll;
+        yq[q] = r < len ? d.yreg[e[q] >> 8] : 0ll;
       }
 #pragma unroll
       for (int q = 0; q < kBatch; ++q)
-        if (r0 + q * 32 + lane < nd.len) {
+        if (r0 + q * 32 + lane < len) {
           const uint32_t w = ent_w<1>(e[q]);
           atomicAdd(&hn[b[q] + (b[q] >> 3)], w);
           atomicAdd(&hs[b[q] + (b[q] >> 3)], static_cast<unsigned long long>(static_cast<long long>(w) * yq[q]));
@@ -456,12 +505,30 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
     }
   }
   __syncwarp();
+}
+
+// Scan of a built histogram.  Lane l owns bins [l*bpl, (l+1)*bpl).  Fills
+// sf[] with the float score of each non-empty candidate bin (-1 otherwise)
+// and returns the warp's best float score (-1 if no valid candidate); with
+// `exact`, also returns in `out` the exact best among the candidates within
+// the screen window.  An empty bin repeats the partition of the nearest
+// non-empty bin below it, which has the lower bin and wins the tie, so empty
+// bins are skipped.
+template <int KIND, int CM>
+__device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, bool exact, int feat,
+                           uint32_t tkey, Cand<CM>& out) {
+  const int lane = threadIdx.x & 31;
+  const int C = d.C, B = d.B;
   const int bpl = (B + 31) >> 5;  // bins per lane (<= 8)
   const int b0 = lane * bpl;
+  const uint32_t* hn = hw;
+  const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(hw + hist_words_n(B));
   Cand<CM> mine;
   mine.valid = false;
+  out.valid = false;
   float sf[8];
   float lmax = -1.0f;
+  float mx;
   if (KIND == 0) {
     uint32_t pre[CM], cum[CM];
 #pragma unroll
@@ -493,17 +560,14 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
             wb += h;
             nL += cum[k];
           }
-        // an empty bin repeats the partition of the nearest non-empty bin
-        // below it, which has the lower bin and wins the tie: skip it
         if (wb > 0u && nL < nd.n) {
           sf[q] = score_class_f<CM>(cum, nd.cp, C, nL, nd.n);
           lmax = fmaxf(lmax, sf[q]);
         }
       }
     }
-    const float mx = warp_max_f(lmax);
-    out.valid = false;
-    if (mx < 0.0f) return;
+    mx = warp_max_f(lmax);
+    if (!exact || mx < 0.0f) return mx;
     const float thr = screen(mx);
 #pragma unroll
     for (int k = 0; k < CM; ++k) cum[k] = pre[k];
@@ -550,15 +614,14 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
         const uint32_t hb = hn[bb + (bb >> 3)];
         cn += hb;
         cs += static_cast<long long>(hs[bb + (bb >> 3)]);
-        if (hb > 0u && cn < nd.n) {  // empty bins repeat a lower bin's partition
+        if (hb > 0u && cn < nd.n) {
           sf[q] = score_reg_f(cs, nd.SP, cn, nd.n);
           lmax = fmaxf(lmax, sf[q]);
         }
       }
     }
-    const float mx = warp_max_f(lmax);
-    out.valid = false;
-    if (mx < 0.0f) return;
+    mx = warp_max_f(lmax);
+    if (!exact || mx < 0.0f) return mx;
     const float thr = screen(mx);
     cn = pn;
     cs = ps;
@@ -580,21 +643,210 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
     }
   }
   warp_select<KIND, CM>(mine, out);
+  return mx;
 }
 
-// Work items of one level's larger nodes: (node, group of G consecutive
-// draw slots), one warp each, spread round-robin over all warps so that a
-// few very large nodes (shallow levels) still occupy the whole GPU.  Each
-// item writes its best candidate; k_finalize reduces them per node.
+template <int KIND, int CM>
+__device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* rows, int feat, uint32_t tkey,
+                              uint32_t* hw, Cand<CM>& out) {
+  build_hist<KIND>(d, nd.base, nd.len, rows, column(d, static_cast<uint32_t>(feat)), hw);
+  scan_hist<KIND, CM>(d, nd, hw, true, feat, tkey, out);
+}
+
+__device__ __forceinline__ bool band_path(const Dev& d, uint32_t nbig) {
+  return d.band_w > 0 && static_cast<uint64_t>(nbig) * static_cast<uint64_t>(d.mtry) <= d.item_cap;
+}
+
+// A feature's exact best candidate, kept as the integers that define it:
+// the node's totals turn them back into the exact score.
+template <int CM>
+struct PackedCand {
+  uint32_t fb;  // feature << 8 | bin, or kLeaf when the feature has no valid split
+  uint32_t nL;
+  uint32_t cL[CM > 1 ? CM : 2];  // class counts, or the target sum's two halves
+};
+
+template <int KIND, int CM>
+__device__ __forceinline__ PackedCand<CM> pack_cand(const Cand<CM>& c) {
+  PackedCand<CM> p;
+  p.fb = c.valid ? ((static_cast<uint32_t>(c.feat) << 8) | static_cast<uint32_t>(c.bin)) : kLeaf;
+  p.nL = c.nL;
+  if (KIND == 1) {
+    p.cL[0] = static_cast<uint32_t>(static_cast<unsigned long long>(c.SL));
+    p.cL[1] = static_cast<uint32_t>(static_cast<unsigned long long>(c.SL) >> 32);
+  } else {
+#pragma unroll
+    for (int k = 0; k < CM; ++k) p.cL[k] = c.cL[k];
+  }
+  return p;
+}
+
+template <int KIND, int CM>
+__device__ __forceinline__ void unpack_cand(const PackedCand<CM>& p, const NodeInfo<CM>& nd, int C, uint32_t tkey,
+                                            Cand<CM>& c) {
+  c.valid = false;
+  if (p.fb == kLeaf) return;
+  if (KIND == 1) {
+    const long long SL = static_cast<long long>(static_cast<unsigned long long>(p.cL[0]) |
+                                                (static_cast<unsigned long long>(p.cL[1]) << 32));
+    make_reg<CM>(c, SL, nd.SP, p.nL, nd.n);
+  } else {
+    make_class<CM>(c, p.cL, nd.cp, C, p.nL, nd.n);
+  }
+  c.feat = static_cast<int32_t>(p.fb >> 8);
+  c.bin = static_cast<int32_t>(p.fb & 255u);
+  c.key = (tkey << 8) | (p.fb & 255u);
+}
+
+// ---------------------------------------------------------------- feature-band path
+// item = rank << 36 | slot << 22 | feature
+__device__ __forceinline__ uint64_t pack_item(uint32_t rank, uint32_t slot, uint32_t f) {
+  return (static_cast<uint64_t>(rank) << 36) | (static_cast<uint64_t>(slot) << 22) | f;
+}
+
+__global__ void __launch_bounds__(256) k_plan_gen(Dev d, int level) {
+  __shared__ uint32_t sband[kMaxBands];
+  const uint32_t nbig = d.work[level];
+  if (!band_path(d, nbig)) return;
+  for (int b = threadIdx.x; b < d.nbands; b += blockDim.x) sband[b] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
+    const uint32_t k = d.big[rank];
+    Perm P;
+    node_perm(d, k, P);
+    for (int s = lane; s < d.mtry; s += 32) {
+      const uint32_t f = perm_apply(P, static_cast<uint32_t>(s));
+      d.items_u[static_cast<uint64_t>(rank) * d.mtry + s] = pack_item(rank, static_cast<uint32_t>(s), f);
+      atomicAdd(&sband[f / static_cast<uint32_t>(d.band_w)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < d.nbands; b += blockDim.x)
+    if (sband[b]) atomicAdd(&d.band_cnt[b], sband[b]);
+}
+
+// exclusive scan of the band counts into band cursors (one block)
+__global__ void k_plan_scan(Dev d, int level) {
+  if (!band_path(d, d.work[level])) return;
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < d.nbands; ++b) {
+      const uint32_t c = d.band_cnt[b];
+      d.band_cnt[b] = run;
+      run += c;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_plan_scatter(Dev d, int level) {
+  const uint32_t nbig = d.work[level];
+  if (!band_path(d, nbig)) return;
+  const uint64_t total = static_cast<uint64_t>(nbig) * d.mtry;
+  const int lane = threadIdx.x & 31;
+  for (uint64_t base = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ull; base < total;
+       base += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint64_t i = base + lane;
+    const bool v = i < total;
+    const uint64_t it = v ? d.items_u[i] : 0ull;
+    const uint32_t band = v ? static_cast<uint32_t>(it & 0x3FFFFFu) / static_cast<uint32_t>(d.band_w) : 0xFFFFFFFFu;
+    // one atomic per distinct band in the warp
+    const unsigned grp = __match_any_sync(kFull, band);
+    const int leader = __ffs(grp) - 1;
+    uint32_t pos = 0;
+    if (v && lane == leader) pos = atomicAdd(&d.band_cnt[band], static_cast<uint32_t>(__popc(grp)));
+    pos = __shfl_sync(kFull, pos, leader);
+    if (v) d.items_s[pos + __popc(grp & lanemask_lt())] = it;
+  }
+}
+
+// one warp per band-sorted item: the feature's exact best candidate, packed
+template <int KIND, int CM>
+__global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band(Dev d, int level) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
+  const uint32_t nbig = d.work[level];
+  if (!band_path(d, nbig)) return;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t* rows_in = d.rows[level & 1];
+  const uint64_t total = static_cast<uint64_t>(nbig) * d.mtry;
+  for (uint64_t i = gwarp; i < total; i += nwarps) {
+    const uint64_t it = d.items_s[i];
+    const uint32_t rank = static_cast<uint32_t>(it >> 36);
+    const uint32_t slot = static_cast<uint32_t>(it >> 22) & 0x3FFFu;
+    const uint32_t f = static_cast<uint32_t>(it & 0x3FFFFFu);
+    NodeInfo<CM> nd;
+    load_node<KIND, CM>(d, d.big[rank], level, nd);
+    build_hist<KIND>(d, nd.base, nd.len, rows_in, column(d, f), hw);
+    Cand<CM> c;
+    scan_hist<KIND, CM>(d, nd, hw, true, static_cast<int>(f), 0u, c);
+    if (lane == 0)
+      reinterpret_cast<PackedCand<CM>*>(d.fbest)[static_cast<uint64_t>(rank) * d.mtry + slot] = pack_cand<KIND, CM>(c);
+  }
+}
+
+// one warp per larger node: exact argmax over the node's per-feature
+// candidates (lanes over draw slots), split record, partition
+template <int KIND, int CM>
+__global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize_band(Dev d, int level) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nbig = d.work[level];
+  if (!band_path(d, nbig)) return;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t* rows_in = d.rows[level & 1];
+  uint32_t* rows_out = d.rows[(level & 1) ^ 1];
+  unsigned long long bytes = 0;
+  for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
+    const uint32_t k = d.big[rank];
+    NodeInfo<CM> nd;
+    load_node<KIND, CM>(d, k, level, nd);
+    const PackedCand<CM>* pc = reinterpret_cast<const PackedCand<CM>*>(d.fbest) + static_cast<uint64_t>(rank) * d.mtry;
+    Cand<CM> best;
+    best.valid = false;
+    for (int s0 = 0; s0 < d.mtry; s0 += 32) {
+      const int s = s0 + lane;
+      Cand<CM> mine;
+      mine.valid = false;
+      if (s < d.mtry) {
+        const PackedCand<CM> p = pc[s];
+        const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(s) : (p.fb >> 8);
+        unpack_cand<KIND, CM>(p, nd, d.C, tkey, mine);
+      }
+      Cand<CM> c;
+      warp_select<KIND, CM>(mine, c);
+      if (better(c, best)) best = c;
+    }
+    uint32_t sp = 0;
+    if (lane == 0) sp = commit_split<KIND, CM>(d, k, best, nd);
+    sp = __shfl_sync(kFull, sp, 0);
+    bytes += static_cast<unsigned long long>(nd.len) * (d.mtry + 4ull + (KIND ? 8ull : 0ull));
+    if (sp == kLeaf) continue;
+    const uint32_t nl = warp_partition(d, nd.base, nd.len, sp, rows_in, rows_out);
+    if (lane == 0) d.nd_lrows[k] = nl;
+    bytes += static_cast<unsigned long long>(nd.len) * 5ull;
+  }
+  if (lane == 0 && bytes) atomicAdd(&d.counters[0], bytes);
+}
+
+// ---------------------------------------------------------------- grouped path
+// Work items of a level's larger nodes: (node, group of G consecutive draw
+// slots), one warp each, spread round-robin over all warps; each item writes
+// its exact best candidate and k_finalize reduces them per node.
 template <int KIND, int CM>
 __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items(Dev d, int level) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
+  const uint32_t nbig = d.work[level];
+  if (band_path(d, nbig)) return;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
-  const uint32_t nbig = d.work[level];
   const int G = (d.mtry + kItemsPerNode - 1) / kItemsPerNode;
   const int ipn = (d.mtry + G - 1) / G;
   Cand<CM>* out = reinterpret_cast<Cand<CM>*>(d.cand);
@@ -606,16 +858,15 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items(Dev 
     NodeInfo<CM> nd;
     load_node<KIND, CM>(d, k, level, nd);
     Perm P;
-    perm_init(P, static_cast<uint32_t>(d.p_aug), d.seed, d.nd_heap[k], unit_word(d.t, d.nd_tree[k]),
-              purpose_word(kPurposeMtry, d.job));
+    node_perm(d, k, P);
     Cand<CM> best;
     best.valid = false;
     const int s1 = min(d.mtry, (part + 1) * G);
     for (int slot = part * G; slot < s1; ++slot) {
-      const int f = static_cast<int>(perm_apply(P, static_cast<uint32_t>(slot)));
-      const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(slot) : static_cast<uint32_t>(f);
+      const uint32_t f = perm_apply(P, static_cast<uint32_t>(slot));
+      const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(slot) : f;
       Cand<CM> c;
-      dense_feature<KIND, CM>(d, nd, rows_in, f, tkey, hw, c);
+      dense_feature<KIND, CM>(d, nd, rows_in, static_cast<int>(f), tkey, hw, c);
       if (better(c, best)) best = c;
     }
     if (lane == 0) out[it] = best;
@@ -623,16 +874,16 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items(Dev 
 }
 
 // One warp per larger node: exact argmax over the node's item candidates,
-// commit, then a stable partition (left rows in order from the front, right
-// rows in order from the back, reversed) with 8 gathers per lane in flight.
+// split record, partition.
 template <int KIND, int CM>
 __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize(Dev d, int level) {
   const int lane = threadIdx.x & 31;
+  const uint32_t nbig = d.work[level];
+  if (band_path(d, nbig)) return;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
   uint32_t* rows_out = d.rows[(level & 1) ^ 1];
-  const uint32_t nbig = d.work[level];
   const int G = (d.mtry + kItemsPerNode - 1) / kItemsPerNode;
   const int ipn = (d.mtry + G - 1) / G;
   const Cand<CM>* cand = reinterpret_cast<const Cand<CM>*>(d.cand);
@@ -651,34 +902,8 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize(Dev d, int 
     sp = __shfl_sync(kFull, sp, 0);
     bytes += static_cast<unsigned long long>(nd.len) * (d.mtry + 4ull + (KIND ? 8ull : 0ull));
     if (sp == kLeaf) continue;
-    const uint8_t* col = d.colptr[sp >> 8];
-    const uint32_t thr = sp & 255u;
-    uint32_t lbase = 0, rbase = 0;
-    const uint32_t lt = lanemask_lt();
-    for (uint32_t r0 = 0; r0 < nd.len; r0 += 256) {
-      uint32_t e[8], b[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t r = r0 + q * 32 + lane;
-        e[q] = r < nd.len ? rows_in[nd.base + r] : 0u;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t r = r0 + q * 32 + lane;
-        b[q] = r < nd.len ? col[e[q] >> 8] : 0u;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const bool v = r0 + q * 32 + lane < nd.len;
-        const bool gl = v && b[q] <= thr, gr = v && !gl;
-        const unsigned bl = __ballot_sync(kFull, gl), br = __ballot_sync(kFull, gr);
-        if (gl) rows_out[nd.base + lbase + __popc(bl & lt)] = e[q];
-        if (gr) rows_out[nd.base + nd.len - 1u - (rbase + __popc(br & lt))] = e[q];
-        lbase += __popc(bl);
-        rbase += __popc(br);
-      }
-    }
-    if (lane == 0) d.nd_lrows[k] = lbase;
+    const uint32_t nl = warp_partition(d, nd.base, nd.len, sp, rows_in, rows_out);
+    if (lane == 0) d.nd_lrows[k] = nl;
     bytes += static_cast<unsigned long long>(nd.len) * 5ull;
   }
   if (lane == 0 && bytes) atomicAdd(&d.counters[0], bytes);
@@ -687,6 +912,14 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize(Dev d, int 
 template <int KIND, int CM>
 void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_t smem, cudaStream_t st) {
   k_split_small<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+  if (d.band_w > 0) {
+    cudaMemsetAsync(d.band_cnt, 0, kMaxBands * sizeof(uint32_t), st);
+    k_plan_gen<<<grid_small, 256, 0, st>>>(d, level);
+    k_plan_scan<<<1, 32, 0, st>>>(d, level);
+    k_plan_scatter<<<grid_small, 256, 0, st>>>(d, level);
+    k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
+    k_finalize_band<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+  }
   k_items<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
   k_finalize<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
 }
@@ -698,6 +931,15 @@ int split_variant(int kind, int C) {
   return C <= 2 ? 0 : (C <= 4 ? 1 : 2);
 }
 
+size_t packed_bytes(int variant) {
+  switch (variant) {
+    case 0: return sizeof(PackedCand<2>);
+    case 1: return sizeof(PackedCand<4>);
+    case 2: return sizeof(PackedCand<8>);
+    default: return sizeof(PackedCand<1>);
+  }
+}
+
 size_t cand_bytes(int variant) {
   switch (variant) {
     case 0: return sizeof(Cand<2>);
@@ -707,13 +949,27 @@ size_t cand_bytes(int variant) {
   }
 }
 
-const void* split_big_ptr(int variant) {
+void split_kernel_ptrs(int variant, const void** ptrs, int* n) {
+  int i = 0;
   switch (variant) {
-    case 0: return reinterpret_cast<const void*>(&k_items<0, 2>);
-    case 1: return reinterpret_cast<const void*>(&k_items<0, 4>);
-    case 2: return reinterpret_cast<const void*>(&k_items<0, 8>);
-    default: return reinterpret_cast<const void*>(&k_items<1, 1>);
+    case 0:
+      ptrs[i++] = reinterpret_cast<const void*>(&k_items<0, 2>);
+      ptrs[i++] = reinterpret_cast<const void*>(&k_items_band<0, 2>);
+      break;
+    case 1:
+      ptrs[i++] = reinterpret_cast<const void*>(&k_items<0, 4>);
+      ptrs[i++] = reinterpret_cast<const void*>(&k_items_band<0, 4>);
+      break;
+    case 2:
+      ptrs[i++] = reinterpret_cast<const void*>(&k_items<0, 8>);
+      ptrs[i++] = reinterpret_cast<const void*>(&k_items_band<0, 8>);
+      break;
+    default:
+      ptrs[i++] = reinterpret_cast<const void*>(&k_items<1, 1>);
+      ptrs[i++] = reinterpret_cast<const void*>(&k_items_band<1, 1>);
+      break;
   }
+  *n = i;
 }
 
 void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st) {

@@ -70,6 +70,9 @@ struct boruta_session {
   // launch geometry
   int sms = 0, split_grid = 0, small_grid = 0, tree_grid = 0, permut_grid = 0;
   size_t split_smem = 0;
+  // second stream for the small-node kernel, and its fork/join events
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   // split-kernel timing of the last step
   std::vector<cudaEvent_t> ev;
   double split_ms = 0.0;
@@ -96,6 +99,12 @@ struct boruta_session {
     if (st) cudaStreamSynchronize(st);
     for (void* q : dev_allocs) cudaFree(q);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (st2) {
+      cudaStreamSynchronize(st2);
+      cudaStreamDestroy(st2);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
     if (status_h) cudaFreeHost(status_h);
     if (state_pin) cudaFreeHost(state_pin);
     if (live_pin) cudaFreeHost(live_pin);
@@ -284,6 +293,14 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   // larger nodes of one level: at most N/33 per tree (each has > 32 rows)
   const size_t big_cap = static_cast<size_t>(n_trees) * (static_cast<size_t>(N) / 33 + 1);
   if ((rc = s->alloc(&d.big, big_cap))) return rc;
+  uint8_t* ninfo = nullptr;
+  if ((rc = s->alloc(&ninfo, big_cap * ninfo_bytes(split_variant(d.kind, d.C))))) return rc;
+  d.ninfo = ninfo;
+  // nodes of one level: at most min(2^D, N) per tree
+  const size_t level_cap = std::min<size_t>(
+      cap, static_cast<size_t>(n_trees) * std::min<uint64_t>(1ull << max_depth, static_cast<uint64_t>(N)));
+  if ((rc = s->alloc(&d.small, level_cap))) return rc;
+  if ((rc = s->alloc(&d.nsmall, max_depth + 2))) return rc;
   uint8_t* cand = nullptr;
   if ((rc = s->alloc(&cand, big_cap * kItemsPerNode * cand_bytes(split_variant(d.kind, d.C))))) return rc;
   d.cand = cand;
@@ -323,6 +340,9 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->permut_grid = 16 * s->sms;
   s->ev.resize(2 * (max_depth + 1));
   for (auto& e : s->ev) CK(cudaEventCreate(&e));
+  CK(cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
   s->state_h.assign(p, 0);
   return 0;
 }
@@ -385,6 +405,7 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   CK(cudaMemsetAsync(d.bootcnt, 0, static_cast<size_t>(d.M) * d.N * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.acc, 0, static_cast<size_t>(d.M) * p_aug * kCsaLimbs * sizeof(long long), st));
   CK(cudaMemsetAsync(d.work, 0, (d.D + 2) * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(d.nsmall, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.lvl_cnt, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.counters, 0, sizeof(unsigned long long), st));
 
@@ -393,7 +414,7 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   launch_bootstrap(d, s->tree_grid, st);
   for (int level = 0; level < d.D; ++level) {
     CK(cudaEventRecord(s->ev[2 * level], st));
-    launch_split(d, level, s->small_grid, s->split_grid, s->split_smem, st);
+    launch_split(d, level, s->small_grid, s->split_grid, s->split_smem, st, s->st2, s->fork, s->join);
     CK(cudaEventRecord(s->ev[2 * level + 1], st));
     launch_children(d, level, st);
   }

@@ -44,6 +44,9 @@ struct Dev {
   uint32_t* work;                // [D + 2] per level: number of nodes in `big`
   uint32_t* chunk;               // [kScanBlocks] per-block split counts
   uint32_t* big;                 // [big_cap] this level's active nodes with > 32 rows
+  uint32_t* small;               // [level_cap] this level's active nodes with <= 32 rows
+  uint32_t* nsmall;              // [D + 2] per level: number of nodes in `small`
+  void* ninfo;                   // [big_cap] node totals of `big`, by rank
   void* cand;                    // [big_cap * kItemsPerNode] best candidate per grouped item
   uint64_t* items_u;             // [item_cap] (node rank, slot, feature) per item, node order
   uint64_t* items_s;             // [item_cap] the same, sorted by feature band
@@ -75,8 +78,12 @@ constexpr uint64_t kMaxItems = 64ull << 20;  // plan buffer capacity (items)
 void launch_validate(const Dev& d, cudaStream_t st);
 void launch_shadow(const Dev& d, cudaStream_t st);
 void launch_bootstrap(const Dev& d, int grid, cudaStream_t st);
-// split.cu: k_split_small (nodes <= 32 rows) then k_split_big on one level
-void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st);
+// split.cu: one level's split search.  Nodes are classified on `st`; the
+// small-node kernel then runs on `st2` while the larger-node kernels run on
+// `st` (fork/join through the two events).
+void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st,
+                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join);
+size_t ninfo_bytes(int variant);
 int split_variant(int kind, int C);
 void split_kernel_ptrs(int variant, const void** ptrs, int* n);  // kernels taking dynamic shared memory
 size_t cand_bytes(int variant);

@@ -381,6 +381,38 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, bool v, uint32_t b,
   warp_select<KIND, CM>(mine, out);
 }
 
+// One thread per node of the level: leaves are marked, active nodes are
+// listed as small (<= 32 rows) or larger (warp-aggregated appends).
+template <int KIND, int CM>
+__global__ void __launch_bounds__(256) k_classify(Dev d, int level) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lcount = d.lvl_cnt[level], loff = d.lvl_off[level];
+  for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < lcount;
+       base += gridDim.x * blockDim.x) {
+    const uint32_t idx = base + lane;
+    int cls = 0;  // 0 none, 1 small, 2 larger
+    uint32_t k = 0;
+    if (idx < lcount) {
+      k = loff + idx;
+      NodeInfo<CM> nd;
+      if (load_node<KIND, CM>(d, k, level, nd))
+        cls = nd.len > 32u ? 2 : 1;
+      else
+        d.nd_split[k] = kLeaf;
+    }
+    const unsigned ms = __ballot_sync(kFull, cls == 1), mb = __ballot_sync(kFull, cls == 2);
+    uint32_t s0 = 0, b0 = 0;
+    if (lane == 0) {
+      if (ms) s0 = atomicAdd(&d.nsmall[level], static_cast<uint32_t>(__popc(ms)));
+      if (mb) b0 = atomicAdd(&d.work[level], static_cast<uint32_t>(__popc(mb)));
+    }
+    s0 = __shfl_sync(kFull, s0, 0);
+    b0 = __shfl_sync(kFull, b0, 0);
+    if (cls == 1) d.small[s0 + __popc(ms & lanemask_lt())] = k;
+    if (cls == 2) d.big[b0 + __popc(mb & lanemask_lt())] = k;
+  }
+}
+
 template <int KIND, int CM>
 __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, int level) {
   const int lane = threadIdx.x & 31;
@@ -388,21 +420,13 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
   uint32_t* rows_out = d.rows[(level & 1) ^ 1];
-  const uint32_t lcount = d.lvl_cnt[level], loff = d.lvl_off[level];
+  const uint32_t ns_nodes = d.nsmall[level];
   const int C = d.C;
   unsigned long long bytes = 0;
-  for (uint32_t idx = gwarp; idx < lcount; idx += nwarps) {
-    const uint32_t k = loff + idx;
+  for (uint32_t idx = gwarp; idx < ns_nodes; idx += nwarps) {
+    const uint32_t k = d.small[idx];
     NodeInfo<CM> nd;
-    const bool act = load_node<KIND, CM>(d, k, level, nd);
-    if (!act) {
-      if (lane == 0) d.nd_split[k] = kLeaf;
-      continue;
-    }
-    if (nd.len > 32u) {  // a larger node: listed for the item kernels
-      if (lane == 0) d.big[atomicAdd(&d.work[level], 1u)] = k;
-      continue;
-    }
+    load_node<KIND, CM>(d, k, level, nd);
     Perm P;
     node_perm(d, k, P);
     const bool v = lane < static_cast<int>(nd.len);
@@ -463,7 +487,8 @@ __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint3
   uint32_t* hn = hw;
   unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + hist_words_n(B));
   if (KIND == 0) {
-    for (int i = lane; i < B * C + (B >> 3) + 1; i += 32) hw[i] = 0u;
+    const int words = (B * C + (B >> 3) + 4) & ~3;  // within the 16-byte aligned per-warp block
+    for (int i = lane; i < (words >> 2); i += 32) reinterpret_cast<uint4*>(hw)[i] = make_uint4(0u, 0u, 0u, 0u);
   } else {
     for (int i = lane; i < B + (B >> 3) + 1; i += 32) {
       hn[i] = 0u;
@@ -704,6 +729,7 @@ __device__ __forceinline__ uint64_t pack_item(uint32_t rank, uint32_t slot, uint
   return (static_cast<uint64_t>(rank) << 36) | (static_cast<uint64_t>(slot) << 22) | f;
 }
 
+template <int KIND, int CM>
 __global__ void __launch_bounds__(256) k_plan_gen(Dev d, int level) {
   __shared__ uint32_t sband[kMaxBands];
   const uint32_t nbig = d.work[level];
@@ -715,6 +741,11 @@ __global__ void __launch_bounds__(256) k_plan_gen(Dev d, int level) {
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
     const uint32_t k = d.big[rank];
+    if (lane == 0) {  // the node's totals, read once here instead of by each of its items
+      NodeInfo<CM> nd;
+      load_node<KIND, CM>(d, k, level, nd);
+      reinterpret_cast<NodeInfo<CM>*>(d.ninfo)[rank] = nd;
+    }
     Perm P;
     node_perm(d, k, P);
     for (int s = lane; s < d.mtry; s += 32) {
@@ -780,7 +811,7 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
     const uint32_t slot = static_cast<uint32_t>(it >> 22) & 0x3FFFu;
     const uint32_t f = static_cast<uint32_t>(it & 0x3FFFFFu);
     NodeInfo<CM> nd;
-    load_node<KIND, CM>(d, d.big[rank], level, nd);
+    nd = reinterpret_cast<const NodeInfo<CM>*>(d.ninfo)[rank];
     build_hist<KIND>(d, nd.base, nd.len, rows_in, column(d, f), hw);
     Cand<CM> c;
     scan_hist<KIND, CM>(d, nd, hw, true, static_cast<int>(f), 0u, c);
@@ -910,11 +941,17 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize(Dev d, int 
 }
 
 template <int KIND, int CM>
-void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_t smem, cudaStream_t st) {
-  k_split_small<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_t smem, cudaStream_t st,
+                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join) {
+  k_classify<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+  // small nodes on st2, concurrently with the larger-node kernels on st
+  cudaEventRecord(fork, st);
+  cudaStreamWaitEvent(st2, fork, 0);
+  k_split_small<KIND, CM><<<grid_small, 256, 0, st2>>>(d, level);
+  cudaEventRecord(join, st2);
   if (d.band_w > 0) {
     cudaMemsetAsync(d.band_cnt, 0, kMaxBands * sizeof(uint32_t), st);
-    k_plan_gen<<<grid_small, 256, 0, st>>>(d, level);
+    k_plan_gen<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
     k_plan_scan<<<1, 32, 0, st>>>(d, level);
     k_plan_scatter<<<grid_small, 256, 0, st>>>(d, level);
     k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
@@ -922,6 +959,7 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_
   }
   k_items<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
   k_finalize<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+  cudaStreamWaitEvent(st, join, 0);
 }
 
 }  // namespace
@@ -972,12 +1010,22 @@ void split_kernel_ptrs(int variant, const void** ptrs, int* n) {
   *n = i;
 }
 
-void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st) {
+void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st,
+                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join) {
   switch (split_variant(d.kind, d.C)) {
-    case 0: launch_level<0, 2>(d, level, grid_small, grid_big, smem, st); break;
-    case 1: launch_level<0, 4>(d, level, grid_small, grid_big, smem, st); break;
-    case 2: launch_level<0, 8>(d, level, grid_small, grid_big, smem, st); break;
-    default: launch_level<1, 1>(d, level, grid_small, grid_big, smem, st); break;
+    case 0: launch_level<0, 2>(d, level, grid_small, grid_big, smem, st, st2, fork, join); break;
+    case 1: launch_level<0, 4>(d, level, grid_small, grid_big, smem, st, st2, fork, join); break;
+    case 2: launch_level<0, 8>(d, level, grid_small, grid_big, smem, st, st2, fork, join); break;
+    default: launch_level<1, 1>(d, level, grid_small, grid_big, smem, st, st2, fork, join); break;
+  }
+}
+
+size_t ninfo_bytes(int variant) {
+  switch (variant) {
+    case 0: return sizeof(NodeInfo<2>);
+    case 1: return sizeof(NodeInfo<4>);
+    case 2: return sizeof(NodeInfo<8>);
+    default: return sizeof(NodeInfo<1>);
   }
 }
 

@@ -25,6 +25,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(N=100_000, p=1000, n_trees=500, max_depth=16, n_bins=256)
+# DRAM bytes (read + write) per k_items_band launch from an ncu capture of the
+# same kernel (profiles/k_items_band_binary_N100000_p1000.md: 50-tree capture
+# of all 16 launches, scaled to 500 trees); None once the kernel changes.
+ITEMS_BAND_TRAFFIC_PER_LAUNCH = 11.1e9
 METRIC = "Boruta iterations/sec (binary N=1e5, p=1000, 500 trees, depth 16, OOB permutation importance)"
 UNIT = "iterations/s"
 
@@ -178,7 +182,8 @@ def run_gpu(args):
         dist.barrier()
     clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_{os.getpid()}.csv")
     proc, fh = start_clock_sampler(clk_path) if rank == 0 else (None, None)
-    step_ms, split_ms, split_bytes = [], 0.0, 0.0
+    step_ms = []
+    ks_tot = dict(hist_ms=0.0, hist_bytes=0.0, split_ms=0.0, split_bytes=0.0, launches=0)
     stream = torch.cuda.current_stream()
     for _ in range(args.steps):
         flush.fill_(1)
@@ -189,10 +194,8 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        ks = S.kernel_stats()
-        split_ms += ks["split_ms"]
-        split_bytes += ks["split_bytes"]
-        launches = ks["split_launches"]
+        for k, v in S.kernel_stats().items():
+            ks_tot[k] += v
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -203,6 +206,31 @@ def run_gpu(args):
     value = world * args.steps / (total_ms / 1000.0)
     res = S.read()
     S.close()
+    del S
+
+    # the same iterations with FP64 per-term arithmetic (identical trees and decisions)
+    other = None
+    if not args.no_other:
+        S2 = boruta.Session(X, y, N=w.N, n_classes=nc, precision=1 - precision, job=rank, **params)
+        fresh2 = S2.read()
+        S2.step()
+        S2.write(fresh2)
+        ms2 = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S2.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms2.append(e0.elapsed_time(e1))
+        res2 = S2.read()
+        S2.close()
+        del S2
+        same = bool((res2["decision"] == res["decision"]).all() and (res2["hits"] == res["hits"]).all())
+        other = {"precision": "fp64 terms" if precision else "fp32 terms",
+                 "value": args.steps / (sum(ms2) / 1000.0), "unit": UNIT, "identical_hits_and_decisions": same}
 
     # end to end through the C ABI with host buffers (upload + K iterations + readback)
     t0 = time.perf_counter()
@@ -217,8 +245,10 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
     peak, peak_kind = peaks()
-    achieved = split_bytes / (split_ms / 1000.0) / 1e9 if split_ms > 0 else 0.0
-    per_step_launches = 3 + 3 * w.max_depth + 2 + 2
+    achieved = ks_tot["hist_bytes"] / (ks_tot["hist_ms"] / 1000.0) / 1e9 if ks_tot["hist_ms"] > 0 else 0.0
+    split_gbs = ks_tot["split_bytes"] / (ks_tot["split_ms"] / 1000.0) / 1e9 if ks_tot["split_ms"] > 0 else 0.0
+    # per step: gather + shadow + 2 bootstrap, 12 per level, 2 permutation importance, stats + decide
+    per_step_launches = 4 + 12 * w.max_depth + 2 + 2
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -229,10 +259,15 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "512 MiB buffer written between timed steps; per-step working set > 1 GB"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
-                     "kernel": "k_split (histogram + split scan + partition)",
-                     "peak_kind": f"{peak_kind} hbm_gbs", "launches": launches * args.steps,
-                     "kernel_ms_per_step": split_ms / args.steps},
+                     "frac": achieved / peak if peak else None,
+                     "traffic": ITEMS_BAND_TRAFFIC_PER_LAUNCH,
+                     "kernel": "k_items_band (feature histograms + exact scan of the larger nodes)",
+                     "peak_kind": f"{peak_kind} hbm_gbs", "launches": int(ks_tot["launches"]),
+                     "kernel_ms_per_step": ks_tot["hist_ms"] / args.steps,
+                     "algorithmic_bytes_per_launch": ks_tot["hist_bytes"] / max(1, ks_tot["launches"])},
+        "split_stage": {"ms_per_step": ks_tot["split_ms"] / args.steps, "achieved_gbs": split_gbs,
+                        "note": "all split kernels of the levels, algorithmic bytes / event time"},
+        "other_form": other,
         "cpu_baseline": cpu_baseline_sample(w) if (world == 1 and not args.no_cpu) else None,
         "e2e": {"value": args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps,
@@ -255,6 +290,7 @@ def main():
     ap.add_argument("--precision", type=int, default=1, help="0 = FP64 terms, 1 = FP32 terms")
     ap.add_argument("--ref-trees", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

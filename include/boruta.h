@@ -152,11 +152,19 @@ int boruta_session_write(boruta_session* s, const int8_t* decision, const int32_
 #define BORUTA_DUMP_LEVELS 8
 int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacity, int64_t* bytes);
 
-/* Timing of the dominant kernel of the last step (for the roofline):
- * total milliseconds and launches of the histogram/split kernel, plus its
- * algorithmic bytes (bin gathers + row-state reads) over those launches. */
-int boruta_session_kernel_stats(boruta_session* s, double* split_ms, int32_t* split_launches,
-                                double* split_bytes);
+/* Timing of the last step, from CUDA events on the session's stream (any
+ * pointer may be NULL):
+ *   hist_ms, hist_bytes  the histogram kernel (one launch per tree level):
+ *                        total milliseconds and algorithmic bytes (one row
+ *                        entry and one bin per (row, feature) pair, plus the
+ *                        target for regression, plus the candidate records)
+ *   launches             number of tree levels (histogram-kernel launches)
+ *   split_ms, split_bytes the whole split stage of the levels (classify,
+ *                        histograms, split records, partition), and its
+ *                        algorithmic bytes (bins per (row, feature) pair, row
+ *                        state once per node, partition traffic). */
+int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* launches, double* hist_bytes,
+                                double* split_ms, double* split_bytes);
 
 void boruta_session_destroy(boruta_session* s);
 

@@ -76,6 +76,7 @@ def lib():
         L.boruta_session_write.argtypes = [vp, vp, vp, vp, vp, ct.c_int32]
         L.boruta_session_dump.argtypes = [vp, i32, vp, i64, ct.POINTER(i64)]
         L.boruta_session_kernel_stats.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int32),
+                                                  ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                                   ct.POINTER(ct.c_double)]
         L.boruta_session_destroy.argtypes = [vp]
         L.boruta_session_destroy.restype = None
@@ -186,9 +187,11 @@ class Session:
         return buf.view(dtype)
 
     def kernel_stats(self):
-        ms, n, b = ct.c_double(), ct.c_int32(), ct.c_double()
-        _check(lib().boruta_session_kernel_stats(self._h, ct.byref(ms), ct.byref(n), ct.byref(b)))
-        return dict(split_ms=ms.value, split_launches=n.value, split_bytes=b.value)
+        hms, n, hb, sms, sb = ct.c_double(), ct.c_int32(), ct.c_double(), ct.c_double(), ct.c_double()
+        _check(lib().boruta_session_kernel_stats(self._h, ct.byref(hms), ct.byref(n), ct.byref(hb), ct.byref(sms),
+                                                 ct.byref(sb)))
+        return dict(hist_ms=hms.value, launches=n.value, hist_bytes=hb.value, split_ms=sms.value,
+                    split_bytes=sb.value)
 
     def close(self):
         if getattr(self, "_h", None):

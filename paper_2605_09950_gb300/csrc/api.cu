@@ -79,6 +79,8 @@ struct boruta_session {
   std::vector<double> level_ms;
   int split_launches = 0;
   double split_bytes = 0.0;
+  std::vector<cudaEvent_t> hev;  // around the histogram kernel of each level
+  double hist_ms = 0.0, hist_bytes = 0.0;
 
   template <typename T>
   int alloc(T** p, size_t count) {
@@ -99,6 +101,7 @@ struct boruta_session {
     if (st) cudaStreamSynchronize(st);
     for (void* q : dev_allocs) cudaFree(q);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : hev) cudaEventDestroy(e);
     if (st2) {
       cudaStreamSynchronize(st2);
       cudaStreamDestroy(st2);
@@ -340,6 +343,8 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->permut_grid = 16 * s->sms;
   s->ev.resize(2 * (max_depth + 1));
   for (auto& e : s->ev) CK(cudaEventCreate(&e));
+  s->hev.resize(2 * (max_depth + 1));
+  for (auto& e : s->hev) CK(cudaEventCreate(&e));
   CK(cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
@@ -407,14 +412,15 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   CK(cudaMemsetAsync(d.work, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.nsmall, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.lvl_cnt, 0, (d.D + 2) * sizeof(uint32_t), st));
-  CK(cudaMemsetAsync(d.counters, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(d.counters, 0, 4 * sizeof(unsigned long long), st));
 
   launch_gather_live(d, st);
   launch_shadow(d, st);
   launch_bootstrap(d, s->tree_grid, st);
   for (int level = 0; level < d.D; ++level) {
     CK(cudaEventRecord(s->ev[2 * level], st));
-    launch_split(d, level, s->small_grid, s->split_grid, s->split_smem, st, s->st2, s->fork, s->join);
+    launch_split(d, level, s->small_grid, s->split_grid, s->split_smem, st, s->st2, s->fork, s->join,
+                 s->hev[2 * level], s->hev[2 * level + 1]);
     CK(cudaEventRecord(s->ev[2 * level + 1], st));
     launch_children(d, level, st);
   }
@@ -426,8 +432,8 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->state_pin, d.state, s->p, cudaMemcpyDeviceToHost, st));
-  unsigned long long bytes = 0;
-  CK(cudaMemcpyAsync(&bytes, d.counters, sizeof bytes, cudaMemcpyDeviceToHost, st));
+  unsigned long long bytes[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(bytes, d.counters, sizeof bytes, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const uint32_t err = s->status_h[0];
   if (err) {
@@ -439,15 +445,19 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
     return fail(BORUTA_EINVAL, "device reported error flags 0x%x", err);
   }
   s->split_ms = 0.0;
+  s->hist_ms = 0.0;
   s->level_ms.assign(d.D + 1, 0.0);
   for (int level = 0; level < d.D; ++level) {
-    float ms = 0.f;
+    float ms = 0.f, hms = 0.f;
     CK(cudaEventElapsedTime(&ms, s->ev[2 * level], s->ev[2 * level + 1]));
+    CK(cudaEventElapsedTime(&hms, s->hev[2 * level], s->hev[2 * level + 1]));
     s->split_ms += ms;
+    s->hist_ms += hms;
     s->level_ms[level] = ms;
   }
   s->split_launches = d.D;
-  s->split_bytes = static_cast<double>(bytes);
+  s->split_bytes = static_cast<double>(bytes[0]);
+  s->hist_bytes = static_cast<double>(bytes[2]);
   std::memcpy(s->state_h.data(), s->state_pin, s->p);
   s->t = t;
   const int32_t und = static_cast<int32_t>(s->status_h[1]);
@@ -495,11 +505,13 @@ int boruta_session_write(boruta_session* s, const int8_t* decision, const int32_
   return 0;
 }
 
-int boruta_session_kernel_stats(boruta_session* s, double* split_ms, int32_t* split_launches,
-                                double* split_bytes) {
+int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* launches, double* hist_bytes,
+                                double* split_ms, double* split_bytes) {
   if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  if (hist_ms) *hist_ms = s->hist_ms;
+  if (launches) *launches = s->split_launches;
+  if (hist_bytes) *hist_bytes = s->hist_bytes;
   if (split_ms) *split_ms = s->split_ms;
-  if (split_launches) *split_launches = s->split_launches;
   if (split_bytes) *split_bytes = s->split_bytes;
   return 0;
 }

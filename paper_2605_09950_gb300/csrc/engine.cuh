@@ -64,7 +64,8 @@ struct Dev {
   double* hist;                  // [max_iter][p]
   double* smax;                  // [max_iter]
   uint32_t* status;              // [0] error flags, [1] undecided count, [2] n_classes seen
-  unsigned long long* counters;  // [0] split-kernel algorithmic bytes, [1] max |y|
+  unsigned long long* counters;  // [0] split-stage algorithmic bytes, [1] max |y|,
+                                 // [2] histogram-kernel algorithmic bytes
 };
 
 constexpr int kScanBlocks = 512;
@@ -81,8 +82,10 @@ void launch_bootstrap(const Dev& d, int grid, cudaStream_t st);
 // split.cu: one level's split search.  Nodes are classified on `st`; the
 // small-node kernel then runs on `st2` while the larger-node kernels run on
 // `st` (fork/join through the two events).
+// hist_start/hist_end are recorded on `st` around the histogram kernel.
 void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st,
-                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join);
+                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hist_start,
+                  cudaEvent_t hist_end);
 size_t ninfo_bytes(int variant);
 int split_variant(int kind, int C);
 void split_kernel_ptrs(int variant, const void** ptrs, int* n);  // kernels taking dynamic shared memory

@@ -805,6 +805,7 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
   const uint64_t total = static_cast<uint64_t>(nbig) * d.mtry;
+  unsigned long long bytes = 0;
   for (uint64_t i = gwarp; i < total; i += nwarps) {
     const uint64_t it = d.items_s[i];
     const uint32_t rank = static_cast<uint32_t>(it >> 36);
@@ -817,7 +818,11 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
     scan_hist<KIND, CM>(d, nd, hw, true, static_cast<int>(f), 0u, c);
     if (lane == 0)
       reinterpret_cast<PackedCand<CM>*>(d.fbest)[static_cast<uint64_t>(rank) * d.mtry + slot] = pack_cand<KIND, CM>(c);
+    // algorithmic bytes: one row entry and one bin per row (+ the target for
+    // regression), and the packed candidate
+    bytes += static_cast<unsigned long long>(nd.len) * (KIND ? 13ull : 5ull) + sizeof(PackedCand<CM>);
   }
+  if (lane == 0 && bytes) atomicAdd(&d.counters[2], bytes);
 }
 
 // one warp per larger node: exact argmax over the node's per-feature
@@ -882,6 +887,7 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items(Dev 
   const int ipn = (d.mtry + G - 1) / G;
   Cand<CM>* out = reinterpret_cast<Cand<CM>*>(d.cand);
   const uint64_t total = static_cast<uint64_t>(nbig) * ipn;
+  unsigned long long bytes = 0;
   for (uint64_t it = gwarp; it < total; it += nwarps) {
     const uint32_t rank = static_cast<uint32_t>(it / ipn);
     const int part = static_cast<int>(it - static_cast<uint64_t>(rank) * ipn);
@@ -901,7 +907,9 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items(Dev 
       if (better(c, best)) best = c;
     }
     if (lane == 0) out[it] = best;
+    bytes += static_cast<unsigned long long>(s1 - part * G) * nd.len * (KIND ? 13ull : 5ull) + sizeof(Cand<CM>);
   }
+  if (lane == 0 && bytes) atomicAdd(&d.counters[2], bytes);
 }
 
 // One warp per larger node: exact argmax over the node's item candidates,
@@ -942,7 +950,8 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize(Dev d, int 
 
 template <int KIND, int CM>
 void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_t smem, cudaStream_t st,
-                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join) {
+                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hist_start,
+                  cudaEvent_t hist_end) {
   k_classify<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   // small nodes on st2, concurrently with the larger-node kernels on st
   cudaEventRecord(fork, st);
@@ -954,10 +963,13 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_
     k_plan_gen<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
     k_plan_scan<<<1, 32, 0, st>>>(d, level);
     k_plan_scatter<<<grid_small, 256, 0, st>>>(d, level);
-    k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
-    k_finalize_band<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   }
+  // the histogram kernel of the level (one of the two does the work)
+  cudaEventRecord(hist_start, st);
+  if (d.band_w > 0) k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
   k_items<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
+  cudaEventRecord(hist_end, st);
+  if (d.band_w > 0) k_finalize_band<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   k_finalize<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   cudaStreamWaitEvent(st, join, 0);
 }
@@ -1011,12 +1023,12 @@ void split_kernel_ptrs(int variant, const void** ptrs, int* n) {
 }
 
 void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st,
-                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join) {
+                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hs, cudaEvent_t he) {
   switch (split_variant(d.kind, d.C)) {
-    case 0: launch_level<0, 2>(d, level, grid_small, grid_big, smem, st, st2, fork, join); break;
-    case 1: launch_level<0, 4>(d, level, grid_small, grid_big, smem, st, st2, fork, join); break;
-    case 2: launch_level<0, 8>(d, level, grid_small, grid_big, smem, st, st2, fork, join); break;
-    default: launch_level<1, 1>(d, level, grid_small, grid_big, smem, st, st2, fork, join); break;
+    case 0: launch_level<0, 2>(d, level, grid_small, grid_big, smem, st, st2, fork, join, hs, he); break;
+    case 1: launch_level<0, 4>(d, level, grid_small, grid_big, smem, st, st2, fork, join, hs, he); break;
+    case 2: launch_level<0, 8>(d, level, grid_small, grid_big, smem, st, st2, fork, join, hs, he); break;
+    default: launch_level<1, 1>(d, level, grid_small, grid_big, smem, st, st2, fork, join, hs, he); break;
   }
 }
 

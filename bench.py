@@ -84,10 +84,10 @@ def stop_clock_sampler(proc, f, path, gpu_index):
             "samples": len(sm)}
 
 
-def workload():
+def workload(trees=None):
     from paper_2605_09950_gb300 import synth
 
-    return synth.binary_wide(N=WORKLOAD["N"], p=WORKLOAD["p"], n_trees=WORKLOAD["n_trees"],
+    return synth.binary_wide(N=WORKLOAD["N"], p=WORKLOAD["p"], n_trees=trees or WORKLOAD["n_trees"],
                              max_depth=WORKLOAD["max_depth"], n_bins=WORKLOAD["n_bins"], max_iter=100)
 
 
@@ -165,7 +165,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    w = workload()
+    w = workload(args.trees)
     X = torch.from_numpy(w.X).cuda()
     y = torch.from_numpy(w.y).cuda()
     params = w.params()
@@ -254,7 +254,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "u8+int64+" + ("f32" if precision else "f64"), "data": "synthetic",
-        "config": {"workload": "binary_N100000_p1000", **WORKLOAD, "importance": "permut_oob",
+        "config": {"workload": "binary_N100000_p1000", **WORKLOAD, "n_trees": w.n_trees,
+                   "importance": "permut_oob",
                    "precision": "fp32 terms, exact sums" if precision else "fp64 terms, exact sums",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "512 MiB buffer written between timed steps; per-step working set > 1 GB"},
@@ -291,6 +292,7 @@ def main():
     ap.add_argument("--ref-trees", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
+    ap.add_argument("--trees", type=int, default=None, help="fewer trees (profiling captures only)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

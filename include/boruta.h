@@ -66,6 +66,8 @@ typedef struct {
   uint32_t job;    /* job id folded into every random stream (batches); default 0 */
   int host_inputs; /* 1: X and y are host pointers, copied to the device inside the call */
   int graph;       /* 1: replay each iteration's level loop as a CUDA graph */
+  int split_path;  /* larger nodes: 0 = feature-band-sorted items when they fit (default),
+                      1 = grouped items only; results are identical */
 } boruta_opts;
 
 /* Host-side, caller-allocated outputs. */

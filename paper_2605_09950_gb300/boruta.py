@@ -39,7 +39,7 @@ class BorutaError(RuntimeError):
 class Opts(ct.Structure):
     _fields_ = [("stat", ct.c_int), ("precision", ct.c_int), ("tie_break", ct.c_int),
                 ("n_classes", ct.c_int), ("kl_eps", ct.c_double), ("stream", ct.c_void_p),
-                ("job", ct.c_uint32), ("host_inputs", ct.c_int), ("graph", ct.c_int)]
+                ("job", ct.c_uint32), ("host_inputs", ct.c_int), ("graph", ct.c_int), ("split_path", ct.c_int)]
 
 
 class Result(ct.Structure):
@@ -105,11 +105,11 @@ def _stream():
 
 
 def make_opts(stat=0, precision=0, tie_break=0, n_classes=0, kl_eps=1e-7, job=0, host_inputs=0,
-              graph=0, stream=None) -> Opts:
+              graph=0, split_path=0, stream=None) -> Opts:
     o = Opts()
     lib().boruta_default_opts(ct.byref(o))
     o.stat, o.precision, o.tie_break, o.n_classes = stat, precision, tie_break, n_classes
-    o.kl_eps, o.job, o.host_inputs, o.graph = kl_eps, job, host_inputs, graph
+    o.kl_eps, o.job, o.host_inputs, o.graph, o.split_path = kl_eps, job, host_inputs, graph, split_path
     o.stream = stream if stream is not None else (None if host_inputs else _stream())
     return o
 

@@ -55,7 +55,7 @@ struct boruta_session {
   Dev d{};
   cudaStream_t st = nullptr;
   int64_t p = 0, N = 0;
-  int task = 0, mtry_opt = 0, max_iter = 0, t = 0;
+  int task = 0, mtry_opt = 0, max_iter = 0, t = 0, split_path = 0;
   bool finished = false;
   std::vector<void*> dev_allocs;
   std::vector<int8_t> state_h;
@@ -130,6 +130,7 @@ static int check_args(const uint8_t* X, int64_t ld, const void* y, int64_t N, in
   if (mtry < 0) return fail(BORUTA_EINVAL, "mtry = %d", mtry);
   if (o->n_classes < 0 || o->n_classes > kMaxClasses)
     return fail(BORUTA_EINVAL, "n_classes = %d outside [0, 8]", o->n_classes);
+  if (o->split_path < 0 || o->split_path > 1) return fail(BORUTA_EINVAL, "opts: split_path takes 0 or 1");
   if (o->precision < 0 || o->precision > 1 || o->tie_break < 0 || o->tie_break > 1 || o->stat < 0 ||
       o->stat > 1)
     return fail(BORUTA_EINVAL, "opts: precision, tie_break and stat take 0 or 1");
@@ -155,6 +156,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->N = N;
   s->task = task;
   s->mtry_opt = mtry;
+  s->split_path = o->split_path;
   s->max_iter = max_iter;
   Dev& d = s->d;
   const bool reg = (task & 1) != 0;
@@ -399,7 +401,7 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   // item holds a 14-bit slot and a 22-bit feature
   d.band_w = 0;
   d.nbands = 0;
-  if (d.item_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
+  if (s->split_path == 0 && d.item_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
     int64_t w = std::max<int64_t>(1, kBandBytes / d.ldN);
     w = std::max<int64_t>(w, (p_aug + kMaxBands - 1) / kMaxBands);
     d.band_w = static_cast<int32_t>(w);

@@ -135,22 +135,24 @@ def multiclass_toeplitz(N=1_000_000, p=500, block=10, n_inf=25, n_classes=5, see
     0.8 inside each block (Toeplitz 0.8^|i-j|), 5 classes drawn from a
     softmax over the first column of the first 25 blocks."""
     rng = np.random.default_rng(np.random.PCG64(seed))
-    F = np.empty((p, N))
-    for b0 in range(0, p, block):
-        F[b0] = rng.standard_normal(N)
-        for k in range(b0 + 1, min(b0 + block, p)):
-            F[k] = 0.8 * F[k - 1] + 0.6 * rng.standard_normal(N)
     inf = np.arange(n_inf) * block
     W = rng.normal(0.0, 1.0 / math.sqrt(n_inf), size=(n_classes, n_inf))
-    logits = W @ F[inf]
+    X = np.zeros((p, pad16(N)), dtype=np.uint8)
+    logits = np.zeros((n_classes, N))
+    col = None
+    for j in range(p):  # column by column: AR(1) inside each block, quantised at once
+        z = rng.standard_normal(N)
+        col = z if j % block == 0 else 0.8 * col + 0.6 * z
+        if j % block == 0 and j // block < n_inf:
+            logits += np.outer(W[:, j // block], col)
+        X[j] = quantise(col[None, :], n_bins)[0]
     logits -= logits.max(axis=0)
     P = np.exp(logits)
     P /= P.sum(axis=0)
     u = rng.random(N)
     y = (u[None, :] > np.cumsum(P, axis=0)).sum(axis=0).clip(0, n_classes - 1).astype(np.uint8)
-    return Workload(f"multiclass_N{N}_p{p}", quantise(F, n_bins), y, N, p,
-                    CLASSIFICATION | importance, n_classes, n_bins, n_trees, max_depth, max_iter,
-                    seed=seed, informative=inf)
+    return Workload(f"multiclass_N{N}_p{p}", X, y, N, p, CLASSIFICATION | importance, n_classes, n_bins,
+                    n_trees, max_depth, max_iter, seed=seed, informative=inf)
 
 
 def batch_jobs(n_jobs=64, seed=4, n_trees=200, max_depth=10, max_iter=50, n_bins=128,

@@ -64,11 +64,11 @@ def compare_nodes(g, o, exact_delta=True, rel=REL32):
         close(g["delta"], o["delta"], rel)
 
 
-def check_iteration(w, trees=None, precision=0, state=None, t=1, tie_break=0):
+def check_iteration(w, trees=None, precision=0, state=None, t=1, tie_break=0, **opts):
     """Runs iteration t on the GPU and checks every dump against the oracle."""
     from paper_2605_09950_gb300 import boruta
 
-    S = session(w, precision=precision, tie_break=tie_break)
+    S = session(w, precision=precision, tie_break=tie_break, **opts)
     p = w.p
     if state is None:
         state = dict(decision=np.zeros(p, np.int8), hits=np.zeros(p, np.int32),
@@ -275,3 +275,96 @@ def test_binary_n100000_p1000_sampled():
     boot = S.dump(boruta.DUMP_BOOT, np.uint32).reshape(w.n_trees, w.N)
     assert (boot.sum(axis=1) == w.N).all()
     assert np.isfinite(imp).all() and (imp >= -1e-15).all()
+
+
+# ---------------------------------------------------------------- larger-node paths
+
+@pytest.mark.parametrize("case", ["binary", "multiclass", "regression"])
+def test_grouped_item_path(case):
+    """The grouped path for larger nodes (used when a level has more items
+    than the band plan holds) gives the same trees and importances."""
+    if case == "binary":
+        w = synth.binary_small(N=800, p=20, n_inf=4, n_trees=8, max_depth=9, max_iter=3)
+    elif case == "multiclass":
+        w = synth.multiclass_toeplitz(N=3000, p=20, block=5, n_inf=3, n_classes=6, n_trees=6, max_depth=8,
+                                      max_iter=3, importance=2)
+    else:
+        w = synth.snp_regression(N=900, p=40, n_add=5, n_pairs=2, n_trees=6, max_depth=7, max_iter=3)
+    check_iteration(w, split_path=1)
+
+
+# ---------------------------------------------------------------- full-size workloads, sampled
+
+def _top_levels(S, P, t, live, sha, trees, L, exact_delta=True):
+    """Nodes above depth L do not depend on what happens below it: the GPU
+    tree's top L levels must equal the oracle tree built with max_depth = L."""
+    from paper_2605_09950_gb300 import boruta
+
+    nodes = S.dump(boruta.DUMP_NODES, boruta.NODE_DTYPE)
+    ptr = S.dump(boruta.DUMP_TREE_PTR, np.int64)
+    saved = P.c.max_depth
+    P.c.max_depth = L
+    try:
+        for tau in trees:
+            nd, _, _ = P.tree(t, live, sha, tau)
+            g = nodes[ptr[tau]:ptr[tau + 1]]
+            g, o = g[g["depth"] < L], nd[nd["depth"] < L]
+            compare_nodes(g, o, exact_delta=exact_delta)
+    finally:
+        P.c.max_depth = saved
+    return nodes, ptr
+
+
+def _importance_properties(S, nodes, ptr, n_trees, permut):
+    from paper_2605_09950_gb300 import boruta
+
+    imp = S.dump(boruta.DUMP_IMP, np.float64).reshape(n_trees, -1)
+    assert np.isfinite(imp).all()
+    for tau in range(n_trees):
+        used = np.unique(nodes["feature"][ptr[tau]:ptr[tau + 1]])
+        used = used[used >= 0]
+        unused = np.setdiff1d(np.arange(imp.shape[1]), used)
+        assert (imp[tau, unused] == 0.0).all()  # never split on: exactly 0 (Alg. 2 and Alg. 3)
+        if not permut and used.size:
+            assert imp[tau].sum() == pytest.approx(1.0, abs=1e-12)
+
+
+def test_snp_regression_n20000_p20000_sampled():
+    """SNP regression N=2e4, p=2e4 (40,000 augmented columns, mtry 13,333),
+    256 trees, depth 12, TreeImp: every shadow column, two bootstrap rows and
+    the top three levels of two trees against the oracle; importance
+    properties of every tree."""
+    from paper_2605_09950_gb300 import boruta
+
+    w = synth.snp_regression(max_iter=3)
+    S = session(w)
+    S.step()
+    P = oracle_problem(w)
+    live = np.arange(w.p, dtype=np.int32)
+    sha = P.shadow(1, live)
+    np.testing.assert_array_equal(S.dump(boruta.DUMP_SHADOW, np.uint8).reshape(sha.shape), sha)
+    boot = S.dump(boruta.DUMP_BOOT, np.uint32).reshape(w.n_trees, w.N)
+    for tau in (0, w.n_trees - 1):
+        np.testing.assert_array_equal(boot[tau], oracle.bootstrap(w.seed, 0, 1, tau, w.N))
+    nodes, ptr = _top_levels(S, P, 1, live, sha, [0, w.n_trees - 1], L=3)
+    _importance_properties(S, nodes, ptr, w.n_trees, permut=False)
+
+
+def test_multiclass_n1000000_p500_sampled():
+    """Five classes, N=1e6, p=500 (Toeplitz blocks), 300 trees, depth 20,
+    Permut: shadows, two bootstrap rows and the top six levels of two trees
+    against the oracle; importance properties of every tree."""
+    from paper_2605_09950_gb300 import boruta
+
+    w = synth.multiclass_toeplitz(max_iter=3)
+    S = session(w, precision=1)
+    S.step()
+    P = oracle_problem(w)
+    live = np.arange(w.p, dtype=np.int32)
+    sha = P.shadow(1, live)
+    np.testing.assert_array_equal(S.dump(boruta.DUMP_SHADOW, np.uint8).reshape(sha.shape), sha)
+    boot = S.dump(boruta.DUMP_BOOT, np.uint32).reshape(w.n_trees, w.N)
+    for tau in (0, w.n_trees - 1):
+        np.testing.assert_array_equal(boot[tau], oracle.bootstrap(w.seed, 0, 1, tau, w.N))
+    nodes, ptr = _top_levels(S, P, 1, live, sha, [0, w.n_trees - 1], L=6, exact_delta=False)  # FP32 form
+    _importance_properties(S, nodes, ptr, w.n_trees, permut=True)

@@ -105,6 +105,33 @@ int boruta_fit(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p
                uint64_t seed, const boruta_opts* opts, boruta_result* out);
 
 /*
+ * boruta_fit_batch -- many independent problems of uneven size (Alg. 1 on
+ * each), run together: every job gets its own CUDA stream and workspace, and
+ * the jobs' iterations are enqueued back to back so that their kernels
+ * overlap on the GPU; a job drops out when it finishes.  Results are those of
+ * boruta_fit on each job with opts->job + j as its job id (the job id keys
+ * all of the job's random streams).
+ *   jobs[j]  one problem, fields as the boruta_fit arguments of that name;
+ *            n_classes overrides opts->n_classes for the job
+ *   opts     shared options (NULL = defaults); opts->stream, if given, is
+ *            waited on before the jobs start
+ *   outs[j]  host result buffers of job j (as boruta_fit's)
+ * On error every job's outputs are unspecified and the message names the
+ * failing job. */
+typedef struct {
+  const uint8_t* X;
+  int64_t ld;
+  const void* y;
+  int64_t N, p;
+  int task, n_trees, max_depth, mtry, n_bins, max_iter;
+  double alpha;
+  uint64_t seed;
+  int n_classes;
+} boruta_job;
+
+int boruta_fit_batch(int n_jobs, const boruta_job* jobs, const boruta_opts* opts, boruta_result* outs);
+
+/*
  * Step-wise interface: the same computation one Boruta iteration at a time
  * (Alg. 1 loop body), for benchmarking, checkpoint/resume and inspection.
  * A session owns its device workspace; X and y must stay valid (device

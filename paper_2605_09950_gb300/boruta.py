@@ -23,7 +23,7 @@ STATUS = {0: "BORUTA_OK", -1: "BORUTA_EINVAL", -2: "BORUTA_EOVERFLOW", -3: "BORU
 
 # the exported symbols of include/boruta.h
 EXPORTS = [
-    "boruta_default_opts", "boruta_fit", "boruta_session_create", "boruta_session_step",
+    "boruta_default_opts", "boruta_fit", "boruta_fit_batch", "boruta_session_create", "boruta_session_step",
     "boruta_session_read", "boruta_session_write", "boruta_session_dump",
     "boruta_session_kernel_stats", "boruta_session_destroy", "boruta_philox", "boruta_perm",
     "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_last_error",
@@ -40,6 +40,13 @@ class Opts(ct.Structure):
     _fields_ = [("stat", ct.c_int), ("precision", ct.c_int), ("tie_break", ct.c_int),
                 ("n_classes", ct.c_int), ("kl_eps", ct.c_double), ("stream", ct.c_void_p),
                 ("job", ct.c_uint32), ("host_inputs", ct.c_int), ("graph", ct.c_int), ("split_path", ct.c_int)]
+
+
+class Job(ct.Structure):
+    _fields_ = [("X", ct.c_void_p), ("ld", ct.c_int64), ("y", ct.c_void_p), ("N", ct.c_int64), ("p", ct.c_int64),
+                ("task", ct.c_int), ("n_trees", ct.c_int), ("max_depth", ct.c_int), ("mtry", ct.c_int),
+                ("n_bins", ct.c_int), ("max_iter", ct.c_int), ("alpha", ct.c_double), ("seed", ct.c_uint64),
+                ("n_classes", ct.c_int)]
 
 
 class Result(ct.Structure):
@@ -70,6 +77,7 @@ def lib():
         L.boruta_default_opts.argtypes = [ct.POINTER(Opts)]
         L.boruta_default_opts.restype = None
         L.boruta_fit.argtypes = fit_args + [ct.POINTER(Result)]
+        L.boruta_fit_batch.argtypes = [i32, ct.POINTER(Job), ct.POINTER(Opts), ct.POINTER(Result)]
         L.boruta_session_create.argtypes = fit_args + [ct.POINTER(vp)]
         L.boruta_session_step.argtypes = [vp, ct.POINTER(ct.c_int32)]
         L.boruta_session_read.argtypes = [vp, vp, vp, vp, vp, ct.POINTER(ct.c_int32)]
@@ -141,6 +149,32 @@ def boruta_fit(X, y, task, n_trees, max_depth, mtry, n_bins, max_iter, alpha, se
                             seed, ct.byref(o), ct.byref(res)))
     del keep
     return dict(decision=dec, hits=hits, imp_history=hist, shadow_max=smax, iterations=res.iterations)
+
+
+def boruta_fit_batch(jobs, **opts):
+    """Many independent problems at once.  jobs: list of dicts with X, y and
+    the boruta_fit parameters (task, n_trees, max_depth, mtry, n_bins,
+    max_iter, alpha, seed, n_classes, N); X/y as for boruta_fit."""
+    host = opts.get("host_inputs", 0)
+    o = make_opts(**opts)
+    arr = (Job * max(1, len(jobs)))()
+    res = (Result * max(1, len(jobs)))()
+    keep, outs = [], []
+    for j, jb in enumerate(jobs):
+        xp, ld, N, p, yp, k = _xy(jb["X"], jb["y"], jb.get("N"), host)
+        keep.append(k)
+        arr[j] = Job(xp, ld, yp, N, p, jb["task"], jb["n_trees"], jb["max_depth"], jb.get("mtry", 0), jb["n_bins"],
+                     jb["max_iter"], jb.get("alpha", 0.01), jb.get("seed", 0), jb.get("n_classes", 0))
+        out = dict(decision=np.zeros(p, np.int8), hits=np.zeros(p, np.int32),
+                   imp_history=np.zeros((jb["max_iter"], p)), shadow_max=np.zeros(jb["max_iter"]))
+        outs.append(out)
+        res[j] = Result(out["decision"].ctypes.data, out["hits"].ctypes.data, out["imp_history"].ctypes.data,
+                        out["shadow_max"].ctypes.data, 0)
+    _check(lib().boruta_fit_batch(len(jobs), arr, ct.byref(o), res))
+    for j, out in enumerate(outs):
+        out["iterations"] = res[j].iterations
+    del keep
+    return outs
 
 
 class Session:

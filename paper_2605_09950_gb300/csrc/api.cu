@@ -56,6 +56,9 @@ struct boruta_session {
   cudaStream_t st = nullptr;
   int64_t p = 0, N = 0;
   int task = 0, mtry_opt = 0, max_iter = 0, t = 0, split_path = 0;
+  int pending_t = 0;  // iteration enqueued and not yet finished
+  bool own_stream = false;
+  unsigned long long* counters_h = nullptr;  // pinned copy of the device counters
   bool finished = false;
   std::vector<void*> dev_allocs;
   std::vector<int8_t> state_h;
@@ -109,6 +112,8 @@ struct boruta_session {
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
     if (status_h) cudaFreeHost(status_h);
+    if (counters_h) cudaFreeHost(counters_h);
+    if (own_stream && st) cudaStreamDestroy(st);
     if (state_pin) cudaFreeHost(state_pin);
     if (live_pin) cudaFreeHost(live_pin);
   }
@@ -247,6 +252,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   d.pascal = pascal;
 
   CK(cudaHostAlloc(&s->status_h, 4 * sizeof(uint32_t), cudaHostAllocDefault));
+  CK(cudaHostAlloc(reinterpret_cast<void**>(&s->counters_h), 4 * sizeof(unsigned long long), cudaHostAllocDefault));
   CK(cudaHostAlloc(&s->state_pin, p, cudaHostAllocDefault));
   CK(cudaHostAlloc(&s->live_pin, p * sizeof(int32_t), cudaHostAllocDefault));
 
@@ -333,9 +339,15 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->split_smem = split_smem_bytes(d.kind, d.C, d.B);
   const void* kptr[4];
   int nk = 0;
-  split_kernel_ptrs(split_variant(d.kind, d.C), kptr, &nk);
+  const int variant = split_variant(d.kind, d.C);
+  split_kernel_ptrs(variant, kptr, &nk);
+  // The limit is a property of the kernel, shared by every session in the
+  // process: set it to what the variant can need at most (its largest class
+  // count, 256 bins) so that no session lowers it below another's launches.
+  const int variant_C[4] = {2, 4, 8, 1};
+  const size_t smem_cap = std::max(s->split_smem, split_smem_bytes(d.kind, variant_C[variant], 256));
   for (int i = 0; i < nk; ++i)
-    CK(cudaFuncSetAttribute(kptr[i], cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(s->split_smem)));
+    CK(cudaFuncSetAttribute(kptr[i], cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_cap)));
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kptr[1], kSplitThreads, s->split_smem));
   if (per_sm < 1) return fail(BORUTA_EINVAL, "split kernel does not fit on an SM");
@@ -378,9 +390,12 @@ int boruta_session_create(const uint8_t* X, int64_t ld, const void* y, int64_t N
   return 0;
 }
 
-int boruta_session_step(boruta_session* s, int32_t* undecided) {
+// Enqueues iteration t+1 on the session's stream, with the copies of its
+// status, state and counters into pinned host memory; does not wait.
+static int step_launch(boruta_session* s) {
   if (!s) return fail(BORUTA_EINVAL, "session is NULL");
   if (s->finished) return fail(BORUTA_EINVAL, "the run is finished (no undecided feature or t = max_iter)");
+  if (s->pending_t) return fail(BORUTA_EINVAL, "an iteration is already in flight");
   Dev& d = s->d;
   cudaStream_t st = s->st;
   const int t = s->t + 1;
@@ -416,27 +431,48 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   CK(cudaMemsetAsync(d.lvl_cnt, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.counters, 0, 4 * sizeof(unsigned long long), st));
 
+#define CK_LAUNCH(what)                                                                          \
+  do {                                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                                         \
+    if (e_ != cudaSuccess) return fail(BORUTA_ECUDA, "launching %s: %s", what, cudaGetErrorString(e_)); \
+  } while (0)
+  CK_LAUNCH("(before the iteration)");
   launch_gather_live(d, st);
+  CK_LAUNCH("k_gather_live");
   launch_shadow(d, st);
+  CK_LAUNCH("k_shadow");
   launch_bootstrap(d, s->tree_grid, st);
+  CK_LAUNCH("bootstrap kernels");
   for (int level = 0; level < d.D; ++level) {
     CK(cudaEventRecord(s->ev[2 * level], st));
     launch_split(d, level, s->small_grid, s->split_grid, s->split_smem, st, s->st2, s->fork, s->join,
                  s->hev[2 * level], s->hev[2 * level + 1]);
+    CK_LAUNCH("split kernels");
     CK(cudaEventRecord(s->ev[2 * level + 1], st));
     launch_children(d, level, st);
+    CK_LAUNCH("next-level kernels");
   }
   if (d.permut)
     launch_permut(d, s->permut_grid, st);
   else
     launch_treeimp(d, s->tree_grid, st);
+  CK_LAUNCH("importance kernels");
   launch_stats_decide(d, st);
-  CK(cudaGetLastError());
+  CK_LAUNCH("k_stats / k_decide");
   CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->state_pin, d.state, s->p, cudaMemcpyDeviceToHost, st));
-  unsigned long long bytes[4] = {0, 0, 0, 0};
-  CK(cudaMemcpyAsync(bytes, d.counters, sizeof bytes, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpyAsync(s->counters_h, d.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  s->pending_t = t;
+  return 0;
+}
+
+// Waits for the iteration enqueued by step_launch and takes its results.
+static int step_finish(boruta_session* s, int32_t* undecided) {
+  Dev& d = s->d;
+  const int t = s->pending_t;
+  s->pending_t = 0;
+  CK(cudaStreamSynchronize(s->st));
+  const unsigned long long* bytes = s->counters_h;
   const uint32_t err = s->status_h[0];
   if (err) {
     s->finished = true;
@@ -466,6 +502,12 @@ int boruta_session_step(boruta_session* s, int32_t* undecided) {
   s->finished = und == 0 || t >= s->max_iter;
   if (undecided) *undecided = und;
   return 0;
+}
+
+int boruta_session_step(boruta_session* s, int32_t* undecided) {
+  int rc = step_launch(s);
+  if (rc) return rc;
+  return step_finish(s, undecided);
 }
 
 int boruta_session_read(boruta_session* s, int8_t* decision, int32_t* hits, double* imp_history,
@@ -650,6 +692,78 @@ int boruta_fit(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p
   std::string msg = g_error;
   boruta_session_destroy(s);
   g_error = msg;
+  return rc;
+}
+
+int boruta_fit_batch(int n_jobs, const boruta_job* jobs, const boruta_opts* opts, boruta_result* outs) {
+  if (n_jobs < 0 || (n_jobs > 0 && (!jobs || !outs))) return fail(BORUTA_EINVAL, "bad batch arguments");
+  for (int j = 0; j < n_jobs; ++j)
+    if (!outs[j].decision || !outs[j].hits || !outs[j].imp_history || !outs[j].shadow_max)
+      return fail(BORUTA_EINVAL, "job %d: result buffers must not be NULL", j);
+  boruta_opts base;
+  if (opts)
+    base = *opts;
+  else
+    boruta_default_opts(&base);
+  cudaStream_t user = static_cast<cudaStream_t>(base.stream);
+  cudaEvent_t ready = nullptr;
+  CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  CK(cudaEventRecord(ready, user));
+  std::vector<boruta_session*> ss(n_jobs, nullptr);
+  int rc = 0;
+  auto cleanup = [&]() {
+    std::string msg = g_error;
+    for (auto* s : ss) boruta_session_destroy(s);
+    cudaEventDestroy(ready);
+    g_error = msg;
+  };
+  for (int j = 0; j < n_jobs && !rc; ++j) {
+    const boruta_job& J = jobs[j];
+    boruta_opts o = base;
+    o.job = base.job + static_cast<uint32_t>(j);
+    o.n_classes = J.n_classes;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamWaitEvent(st, ready, 0) != cudaSuccess) {
+      rc = fail(BORUTA_ECUDA, "job %d: stream creation failed", j);
+      if (st) cudaStreamDestroy(st);
+      break;
+    }
+    o.stream = st;
+    rc = boruta_session_create(J.X, J.ld, J.y, J.N, J.p, J.task, J.n_trees, J.max_depth, J.mtry, J.n_bins,
+                               J.max_iter, J.alpha, J.seed, &o, &ss[j]);
+    if (rc) {
+      cudaStreamDestroy(st);
+      fail(rc, "job %d: %s", j, std::string(g_error).c_str());
+      break;
+    }
+    ss[j]->own_stream = true;
+  }
+  // lockstep: enqueue one iteration of every unfinished job, then collect them
+  while (!rc) {
+    std::vector<int> active;
+    for (int j = 0; j < n_jobs; ++j)
+      if (!ss[j]->finished) active.push_back(j);
+    if (active.empty()) break;
+    for (int j : active) {
+      if ((rc = step_launch(ss[j]))) {
+        fail(rc, "job %d: %s", j, std::string(g_error).c_str());
+        break;
+      }
+    }
+    for (int j : active) {
+      if (!ss[j]->pending_t) continue;
+      int32_t und = 0;
+      const int r = step_finish(ss[j], &und);
+      if (r && !rc) rc = fail(r, "job %d: %s", j, std::string(g_error).c_str());
+    }
+  }
+  for (int j = 0; j < n_jobs && !rc; ++j) {
+    int32_t t = 0;
+    rc = boruta_session_read(ss[j], outs[j].decision, outs[j].hits, outs[j].imp_history, outs[j].shadow_max, &t);
+    outs[j].iterations = t;
+  }
+  cleanup();
   return rc;
 }
 

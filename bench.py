@@ -26,9 +26,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(N=100_000, p=1000, n_trees=500, max_depth=16, n_bins=256)
 # DRAM bytes (read + write) per k_items_band launch from an ncu capture of the
-# same kernel (profiles/k_items_band_binary_N100000_p1000.md: 50-tree capture
-# of all 16 launches, scaled to 500 trees); None once the kernel changes.
-ITEMS_BAND_TRAFFIC_PER_LAUNCH = 11.1e9
+# same kernel (profiles/k_items_band_binary_N100000_p1000.md), scaled to 500
+# trees; None until the current kernel has been captured.
+ITEMS_BAND_TRAFFIC_PER_LAUNCH = None
 METRIC = "Boruta iterations/sec (binary N=1e5, p=1000, 500 trees, depth 16, OOB permutation importance)"
 UNIT = "iterations/s"
 
@@ -196,6 +196,7 @@ def run_gpu(args):
         step_ms.append(e0.elapsed_time(e1))
         for k, v in S.kernel_stats().items():
             ks_tot[k] += v
+    levels = S.dump(boruta.DUMP_LEVELS, np.float64).reshape(-1, 3)
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -265,9 +266,12 @@ def run_gpu(args):
                      "kernel": "k_items_band (feature histograms + exact scan of the larger nodes)",
                      "peak_kind": f"{peak_kind} hbm_gbs", "launches": int(ks_tot["launches"]),
                      "kernel_ms_per_step": ks_tot["hist_ms"] / args.steps,
-                     "algorithmic_bytes_per_launch": ks_tot["hist_bytes"] / max(1, ks_tot["launches"])},
+                     "algorithmic_bytes_per_launch": ks_tot["hist_bytes"] / max(1, ks_tot["launches"]),
+                     "algorithmic_bytes": "per node and level: rows x (mtry bins + 10 B row state)"},
         "split_stage": {"ms_per_step": ks_tot["split_ms"] / args.steps, "achieved_gbs": split_gbs,
-                        "note": "all split kernels of the levels, algorithmic bytes / event time"},
+                        "note": "all split kernels of the levels, algorithmic bytes / event time",
+                        "levels": [[int(c), round(float(a), 3), round(float(h), 3)] for c, a, h in levels[:-1]],
+                        "levels_note": "last timed step, per depth: nodes, split-stage ms, histogram-kernel ms"},
         "other_form": other,
         "cpu_baseline": cpu_baseline_sample(w) if (world == 1 and not args.no_cpu) else None,
         "e2e": {"value": args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,

@@ -167,8 +167,9 @@ int boruta_session_write(boruta_session* s, const int8_t* decision, const int32_
  *   BORUTA_DUMP_NODES    boruta_node [count]  trees in order, each in (depth, heap) order
  *   BORUTA_DUMP_TREE_PTR int64  [M + 1]       offsets of each tree in the node dump
  *   BORUTA_DUMP_LIVE     int32  [p_live]      original columns in play
- *   BORUTA_DUMP_LEVELS   double [max_depth+1][2]  nodes at each depth, milliseconds
- *                        of the split kernel at that depth (0 for the last)
+ *   BORUTA_DUMP_LEVELS   double [max_depth+1][3]  nodes at each depth, milliseconds
+ *                        of the whole split stage at that depth, milliseconds
+ *                        of its histogram kernels (0 for the last depth)
  * host must hold capacity bytes; *bytes receives the size needed (pass
  * host = NULL to query).  */
 #define BORUTA_DUMP_SHADOW 1

@@ -79,7 +79,7 @@ struct boruta_session {
   // split-kernel timing of the last step
   std::vector<cudaEvent_t> ev;
   double split_ms = 0.0;
-  std::vector<double> level_ms;
+  std::vector<double> level_ms, level_hist_ms;
   int split_launches = 0;
   double split_bytes = 0.0;
   std::vector<cudaEvent_t> hev;  // around the histogram kernel of each level
@@ -327,7 +327,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
     uint8_t* fb = nullptr;
     if ((rc = s->alloc(&fb, cap_items * packed_bytes(split_variant(d.kind, d.C))))) return rc;
     d.fbest = fb;
-    if ((rc = s->alloc(&d.band_cnt, kMaxBands))) return rc;
+    if ((rc = s->alloc(&d.band_cnt, kMaxBands + 1))) return rc;
   }
   (void)Cmax;
   CK(cudaMemsetAsync(d.status, 0, 4 * sizeof(uint32_t), s->st));
@@ -485,6 +485,7 @@ static int step_finish(boruta_session* s, int32_t* undecided) {
   s->split_ms = 0.0;
   s->hist_ms = 0.0;
   s->level_ms.assign(d.D + 1, 0.0);
+  s->level_hist_ms.assign(d.D + 1, 0.0);
   for (int level = 0; level < d.D; ++level) {
     float ms = 0.f, hms = 0.f;
     CK(cudaEventElapsedTime(&ms, s->ev[2 * level], s->ev[2 * level + 1]));
@@ -492,6 +493,7 @@ static int step_finish(boruta_session* s, int32_t* undecided) {
     s->split_ms += ms;
     s->hist_ms += hms;
     s->level_ms[level] = ms;
+    s->level_hist_ms[level] = hms;
   }
   s->split_launches = d.D;
   s->split_bytes = static_cast<double>(bytes[0]);
@@ -594,7 +596,7 @@ int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacit
     case BORUTA_DUMP_LIVE:
       return copy_out(s, s->live_d, static_cast<int64_t>(d.p_live) * 4, host, capacity, bytes);
     case BORUTA_DUMP_LEVELS: {
-      const int64_t need = static_cast<int64_t>(d.D + 1) * 2 * 8;
+      const int64_t need = static_cast<int64_t>(d.D + 1) * 3 * 8;
       if (bytes) *bytes = need;
       if (!host) return 0;
       if (capacity < need) return fail(BORUTA_EINVAL, "capacity too small");
@@ -602,8 +604,10 @@ int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacit
       CK(cudaMemcpy(cnt.data(), d.lvl_cnt, (d.D + 2) * 4, cudaMemcpyDeviceToHost));
       double* o = static_cast<double*>(host);
       for (int l = 0; l <= d.D; ++l) {
-        o[2 * l] = cnt[l];
-        o[2 * l + 1] = l < static_cast<int>(s->level_ms.size()) ? s->level_ms[l] : 0.0;
+        const bool timed = l < static_cast<int>(s->level_ms.size());
+        o[3 * l] = cnt[l];
+        o[3 * l + 1] = timed ? s->level_ms[l] : 0.0;
+        o[3 * l + 2] = timed ? s->level_hist_ms[l] : 0.0;
       }
       return 0;
     }

@@ -48,10 +48,11 @@ struct Dev {
   uint32_t* nsmall;              // [D + 2] per level: number of nodes in `small`
   void* ninfo;                   // [big_cap] node totals of `big`, by rank
   void* cand;                    // [big_cap * kItemsPerNode] best candidate per grouped item
-  uint64_t* items_u;             // [item_cap] (node rank, slot, feature) per item, node order
-  uint64_t* items_s;             // [item_cap] the same, sorted by feature band
+  uint64_t* items_u;             // [item_cap] (node rank, slot, feature) per item; each node's
+                                 //   mtry items together, ordered by feature band
+  uint64_t* items_s;             // [item_cap] groups (node rank, first item, count), by band
   void* fbest;                   // [item_cap] packed best candidate per (node rank, slot)
-  uint32_t* band_cnt;            // [kMaxBands] band sizes, then cursors
+  uint32_t* band_cnt;            // [kMaxBands + 1] groups per band, then cursors; last: total
   uint64_t item_cap;
   int32_t band_w, nbands;        // columns per band (0: grouped path only), bands
   // ---- importance and Boruta state
@@ -74,6 +75,15 @@ constexpr int kItemsPerNode = 16;  // work items (groups of draw slots) per larg
 constexpr int kMaxBands = 256;     // feature bands of the band-sorted path
 constexpr int64_t kBandBytes = 24ll << 20;  // column bytes per band (kept in L2 while in use)
 constexpr uint64_t kMaxItems = 64ull << 20;  // plan buffer capacity (items)
+#ifndef BORUTA_STAGED_ROWS
+#define BORUTA_STAGED_ROWS 128
+#endif
+constexpr uint32_t kRegRows = BORUTA_STAGED_ROWS;  // node rows a warp stages in shared memory
+constexpr uint32_t kGroupWork = 8192;        // row x feature work per group for larger nodes
+// row state the method moves per row and tree level besides the bins: the
+// row's entry read and rewritten by the partition (4 + 4 B), its weight and
+// label (1 + 1 B), or weight and 8-byte fixed-point target (regression)
+constexpr uint32_t kRowStateClass = 10, kRowStateReg = 17;
 
 // launchers (kernels.cu)
 void launch_validate(const Dev& d, cudaStream_t st);
@@ -102,10 +112,14 @@ void launch_stats_decide(const Dev& d, cudaStream_t st);
 //   classification: count(b, k) at word b*C + k + b/8
 //   regression:     weight(b) at word b + b/8; sum(b) at u64 b + b/8 after the weights
 __host__ __device__ inline int hist_words_n(int B) { return (B + (B >> 3) + 2) & ~1; }
-__host__ __device__ inline size_t split_smem_per_warp(int kind, int C, int B) {
+__host__ __device__ inline size_t hist_smem_per_warp(int kind, int C, int B) {
   const size_t b = kind == 0 ? (static_cast<size_t>(B) * C + (B >> 3) + 1) * 4
                              : static_cast<size_t>(hist_words_n(B)) * 4 + static_cast<size_t>(B + (B >> 3) + 1) * 8;
   return (b + 15) & ~static_cast<size_t>(15);
+}
+// per warp: the histogram, then a node's row entries (up to kRegRows)
+__host__ __device__ inline size_t split_smem_per_warp(int kind, int C, int B) {
+  return hist_smem_per_warp(kind, C, B) + kRegRows * 4;
 }
 __host__ __device__ inline size_t split_smem_bytes(int kind, int C, int B) {
   return (kSplitThreads / 32) * split_smem_per_warp(kind, C, B);

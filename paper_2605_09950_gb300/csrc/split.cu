@@ -119,24 +119,41 @@ struct NodeInfo {
 };
 
 // ---- scores
+// Exact u32 -> float for v < 2^24 on the integer and FP32 pipes: the bits
+// 0x4B000000 | m are the float 2^23 + m for m < 2^23.
+__device__ __forceinline__ float u24_to_float(uint32_t v) {
+  const float b = __uint_as_float(0x4B000000u | (v & 0x7FFFFFu));
+  return (v & 0x800000u) ? b : b - 8388608.0f;
+}
+
+// |v| as float for a 64-bit v, from three exact 22-bit pieces (all terms
+// non-negative: relative error below 2^-22)
+__device__ __forceinline__ float abs_i64_to_float(long long v) {
+  const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+  return (u24_to_float(static_cast<uint32_t>(a >> 44)) * 17592186044416.0f +
+          u24_to_float(static_cast<uint32_t>(a >> 22) & 0x3FFFFFu) * 4194304.0f) +
+         u24_to_float(static_cast<uint32_t>(a) & 0x3FFFFFu);
+}
+
+// Float scores of the pre-screen (counts and n below 2^24, so the integer
+// inputs convert exactly).  Relative error below 2^-20.
 template <int CM>
 __device__ __forceinline__ float score_class_f(const uint32_t* cl, const uint32_t* cp, int C, uint32_t nL,
                                                uint32_t n) {
-  uint64_t AL = 0, AR = 0;
+  float AL = 0.0f, AR = 0.0f;
 #pragma unroll
   for (int k = 0; k < CM; ++k)
     if (k < C) {
-      const uint64_t l = cl[k], r = cp[k] - cl[k];
+      const float l = u24_to_float(cl[k]), r = u24_to_float(cp[k] - cl[k]);
       AL += l * l;
       AR += r * r;
     }
-  return __fdividef(static_cast<float>(AL), static_cast<float>(nL)) +
-         __fdividef(static_cast<float>(AR), static_cast<float>(n - nL));
+  return __fdividef(AL, u24_to_float(nL)) + __fdividef(AR, u24_to_float(n - nL));
 }
 
 __device__ __forceinline__ float score_reg_f(long long SL, long long SP, uint32_t nL, uint32_t n) {
-  const float l = static_cast<float>(SL), r = static_cast<float>(SP - SL);
-  return __fdividef(l * l, static_cast<float>(nL)) + __fdividef(r * r, static_cast<float>(n - nL));
+  const float l = abs_i64_to_float(SL), r = abs_i64_to_float(SP - SL);
+  return __fdividef(l * l, u24_to_float(nL)) + __fdividef(r * r, u24_to_float(n - nL));
 }
 
 template <int CM>
@@ -172,7 +189,7 @@ __device__ __forceinline__ void make_reg(Cand<CM>& c, long long SL, long long SP
   c.valid = true;
 }
 
-// Relative window of the float pre-screen.  A float score is within 2^-21 of
+// Relative window of the float pre-screen.  A float score is within 2^-20 of
 // the exact score, so every candidate whose exact score is the maximum has a
 // float score above (1 - 2^-16) * (best float score); only those are compared
 // exactly.
@@ -475,6 +492,59 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
 }
 
 // ============================================================ larger nodes
+template <int KIND>
+__device__ __forceinline__ void hist_clear(const Dev& d, uint32_t* hw) {
+  const int lane = threadIdx.x & 31;
+  const int C = d.C, B = d.B;
+  if (KIND == 0) {
+    const int words = (B * C + (B >> 3) + 4) & ~3;  // within the 16-byte aligned per-warp block
+    for (int i = lane; i < (words >> 2); i += 32) reinterpret_cast<uint4*>(hw)[i] = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    uint32_t* hn = hw;
+    unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + hist_words_n(B));
+    for (int i = lane; i < B + (B >> 3) + 1; i += 32) {
+      hn[i] = 0u;
+      hs[i] = 0ull;
+    }
+  }
+}
+
+// Adds up to 32 * kBatch rows, entries already in registers (entry q of
+// lane l is row r0 + q * 32 + l of the node), to the warp's histogram.
+template <int KIND, int kBatch>
+__device__ __forceinline__ void hist_add(const Dev& d, uint32_t r0, uint32_t len, const uint32_t (&e)[kBatch],
+                                         const uint8_t* col, uint32_t* hw) {
+  const int lane = threadIdx.x & 31;
+  const int C = d.C, B = d.B;
+  uint32_t b[kBatch];
+#pragma unroll
+  for (int q = 0; q < kBatch; ++q) {
+    const uint32_t r = r0 + q * 32 + lane;
+    b[q] = r < len ? col[e[q] >> 8] : 0u;
+  }
+  if (KIND == 0) {
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q)
+      if (r0 + q * 32 + lane < len) atomicAdd(&hw[b[q] * C + ent_y(e[q]) + (b[q] >> 3)], ent_w<0>(e[q]));
+  } else {
+    uint32_t* hn = hw;
+    unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + hist_words_n(B));
+    long long yq[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const uint32_t r = r0 + q * 32 + lane;
+      yq[q] = r < len ? d.yreg[e[q] >> 8] : 0ll;
+    }
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q)
+      if (r0 + q * 32 + lane < len) {
+        const uint32_t w = ent_w<1>(e[q]);
+        atomicAdd(&hn[b[q] + (b[q] >> 3)], w);
+        atomicAdd(&hs[b[q] + (b[q] >> 3)], static_cast<unsigned long long>(static_cast<long long>(w) * yq[q]));
+      }
+  }
+}
+
 // Warp-private histogram of one feature over a node's rows.  Rows are
 // gathered 8 per lane per pass so that 8 independent loads per lane are in
 // flight.
@@ -482,63 +552,36 @@ template <int KIND>
 __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint32_t* rows, const uint8_t* col,
                            uint32_t* hw) {
   const int lane = threadIdx.x & 31;
-  const int C = d.C, B = d.B;
   constexpr int kBatch = 8;
-  uint32_t* hn = hw;
-  unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + hist_words_n(B));
-  if (KIND == 0) {
-    const int words = (B * C + (B >> 3) + 4) & ~3;  // within the 16-byte aligned per-warp block
-    for (int i = lane; i < (words >> 2); i += 32) reinterpret_cast<uint4*>(hw)[i] = make_uint4(0u, 0u, 0u, 0u);
-  } else {
-    for (int i = lane; i < B + (B >> 3) + 1; i += 32) {
-      hn[i] = 0u;
-      hs[i] = 0ull;
-    }
+  hist_clear<KIND>(d, hw);
+  uint32_t e[kBatch];
+#pragma unroll
+  for (int q = 0; q < kBatch; ++q) {
+    const uint32_t r = q * 32 + lane;
+    e[q] = r < len ? rows[base + r] : 0u;
   }
   __syncwarp();
   for (uint32_t r0 = 0; r0 < len; r0 += 32 * kBatch) {
-    uint32_t e[kBatch];
-    uint32_t b[kBatch];
-#pragma unroll
-    for (int q = 0; q < kBatch; ++q) {
-      const uint32_t r = r0 + q * 32 + lane;
-      e[q] = r < len ? rows[base + r] : 0u;
-    }
-#pragma unroll
-    for (int q = 0; q < kBatch; ++q) {
-      const uint32_t r = r0 + q * 32 + lane;
-      b[q] = r < len ? col[e[q] >> 8] : 0u;
-    }
-    if (KIND == 0) {
-#pragma unroll
-      for (int q = 0; q < kBatch; ++q)
-        if (r0 + q * 32 + lane < len) atomicAdd(&hw[b[q] * C + ent_y(e[q]) + (b[q] >> 3)], ent_w<0>(e[q]));
-    } else {
-      long long yq[kBatch];
+    if (r0 > 0) {
 #pragma unroll
       for (int q = 0; q < kBatch; ++q) {
         const uint32_t r = r0 + q * 32 + lane;
-        yq[q] = r < len ? d.yreg[e[q] >> 8] : 0ll;
+        e[q] = r < len ? rows[base + r] : 0u;
       }
-#pragma unroll
-      for (int q = 0; q < kBatch; ++q)
-        if (r0 + q * 32 + lane < len) {
-          const uint32_t w = ent_w<1>(e[q]);
-          atomicAdd(&hn[b[q] + (b[q] >> 3)], w);
-          atomicAdd(&hs[b[q] + (b[q] >> 3)], static_cast<unsigned long long>(static_cast<long long>(w) * yq[q]));
-        }
     }
+    hist_add<KIND, kBatch>(d, r0, len, e, col, hw);
   }
   __syncwarp();
 }
 
-// Scan of a built histogram.  Lane l owns bins [l*bpl, (l+1)*bpl).  Fills
-// sf[] with the float score of each non-empty candidate bin (-1 otherwise)
-// and returns the warp's best float score (-1 if no valid candidate); with
+// Scan of a built histogram.  Lane l owns bins [l*bpl, (l+1)*bpl).
+// Returns the warp's best float score (-1 if no valid candidate); with
 // `exact`, also returns in `out` the exact best among the candidates within
 // the screen window.  An empty bin repeats the partition of the nearest
 // non-empty bin below it, which has the lower bin and wins the tie, so empty
-// bins are skipped.
+// bins are skipped: a lane visits only its non-empty bins (a bit mask), and
+// only a lane whose own best float score is inside the window revisits them
+// for the exact comparison.
 template <int KIND, int CM>
 __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, bool exact, int feat,
                            uint32_t tkey, Cand<CM>& out) {
@@ -551,9 +594,8 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
   Cand<CM> mine;
   mine.valid = false;
   out.valid = false;
-  float sf[8];
   float lmax = -1.0f;
-  float mx;
+  uint32_t mask = 0;  // non-empty bins of the lane that can be thresholds
   if (KIND == 0) {
     uint32_t pre[CM], cum[CM];
 #pragma unroll
@@ -561,9 +603,15 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
     for (int q = 0; q < bpl; ++q) {
       const int bb = b0 + q;
       if (bb < B) {
+        uint32_t wb = 0;
 #pragma unroll
         for (int k = 0; k < CM; ++k)
-          if (k < C) pre[k] += hw[bb * C + k + (bb >> 3)];
+          if (k < C) {
+            const uint32_t h = hw[bb * C + k + (bb >> 3)];
+            pre[k] += h;
+            wb += h;
+          }
+        if (wb > 0u && bb < B - 1) mask |= 1u << q;
       }
     }
 #pragma unroll
@@ -571,35 +619,25 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
       pre[k] = warp_excl_scan_u32(pre[k], lane);
       cum[k] = pre[k];
     }
+    for (uint32_t m = mask; m; m &= m - 1) {
+      const int bb = b0 + __ffs(m) - 1;
+      uint32_t nL = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      sf[q] = -1.0f;
-      const int bb = b0 + q;
-      if (q < bpl && bb < B - 1) {
-        uint32_t nL = 0, wb = 0;
-#pragma unroll
-        for (int k = 0; k < CM; ++k)
-          if (k < C) {
-            const uint32_t h = hw[bb * C + k + (bb >> 3)];
-            cum[k] += h;
-            wb += h;
-            nL += cum[k];
-          }
-        if (wb > 0u && nL < nd.n) {
-          sf[q] = score_class_f<CM>(cum, nd.cp, C, nL, nd.n);
-          lmax = fmaxf(lmax, sf[q]);
+      for (int k = 0; k < CM; ++k)
+        if (k < C) {
+          cum[k] += hw[bb * C + k + (bb >> 3)];
+          nL += cum[k];
         }
-      }
+      if (nL < nd.n) lmax = fmaxf(lmax, score_class_f<CM>(cum, nd.cp, C, nL, nd.n));
     }
-    mx = warp_max_f(lmax);
+    const float mx = warp_max_f(lmax);
     if (!exact || mx < 0.0f) return mx;
     const float thr = screen(mx);
+    if (lmax >= thr) {
 #pragma unroll
-    for (int k = 0; k < CM; ++k) cum[k] = pre[k];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int bb = b0 + q;
-      if (q < bpl && bb < B - 1) {
+      for (int k = 0; k < CM; ++k) cum[k] = pre[k];
+      for (uint32_t m = mask; m; m &= m - 1) {
+        const int bb = b0 + __ffs(m) - 1;
         uint32_t nL = 0;
 #pragma unroll
         for (int k = 0; k < CM; ++k)
@@ -607,7 +645,7 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
             cum[k] += hw[bb * C + k + (bb >> 3)];
             nL += cum[k];
           }
-        if (sf[q] >= 0.0f && sf[q] >= thr) {
+        if (nL < nd.n && score_class_f<CM>(cum, nd.cp, C, nL, nd.n) >= thr) {
           Cand<CM> c;
           make_class<CM>(c, cum, nd.cp, C, nL, nd.n);
           c.feat = feat;
@@ -617,46 +655,41 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
         }
       }
     }
+    warp_select<KIND, CM>(mine, out);
+    return mx;
   } else {
     uint32_t tn = 0;
     long long ts = 0;
     for (int q = 0; q < bpl; ++q) {
       const int bb = b0 + q;
       if (bb < B) {
-        tn += hn[bb + (bb >> 3)];
+        const uint32_t h = hn[bb + (bb >> 3)];
+        tn += h;
         ts += static_cast<long long>(hs[bb + (bb >> 3)]);
+        if (h > 0u && bb < B - 1) mask |= 1u << q;
       }
     }
     const uint32_t pn = warp_excl_scan_u32(tn, lane);
     const long long ps = warp_excl_scan_i64(ts, lane);
     uint32_t cn = pn;
     long long cs = ps;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      sf[q] = -1.0f;
-      const int bb = b0 + q;
-      if (q < bpl && bb < B - 1) {
-        const uint32_t hb = hn[bb + (bb >> 3)];
-        cn += hb;
-        cs += static_cast<long long>(hs[bb + (bb >> 3)]);
-        if (hb > 0u && cn < nd.n) {
-          sf[q] = score_reg_f(cs, nd.SP, cn, nd.n);
-          lmax = fmaxf(lmax, sf[q]);
-        }
-      }
+    for (uint32_t m = mask; m; m &= m - 1) {
+      const int bb = b0 + __ffs(m) - 1;
+      cn += hn[bb + (bb >> 3)];
+      cs += static_cast<long long>(hs[bb + (bb >> 3)]);
+      if (cn < nd.n) lmax = fmaxf(lmax, score_reg_f(cs, nd.SP, cn, nd.n));
     }
-    mx = warp_max_f(lmax);
+    const float mx = warp_max_f(lmax);
     if (!exact || mx < 0.0f) return mx;
     const float thr = screen(mx);
-    cn = pn;
-    cs = ps;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int bb = b0 + q;
-      if (q < bpl && bb < B - 1) {
+    if (lmax >= thr) {
+      cn = pn;
+      cs = ps;
+      for (uint32_t m = mask; m; m &= m - 1) {
+        const int bb = b0 + __ffs(m) - 1;
         cn += hn[bb + (bb >> 3)];
         cs += static_cast<long long>(hs[bb + (bb >> 3)]);
-        if (sf[q] >= 0.0f && sf[q] >= thr) {
+        if (cn < nd.n && score_reg_f(cs, nd.SP, cn, nd.n) >= thr) {
           Cand<CM> c;
           make_reg<CM>(c, cs, nd.SP, cn, nd.n);
           c.feat = feat;
@@ -666,9 +699,9 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
         }
       }
     }
+    warp_select<KIND, CM>(mine, out);
+    return mx;
   }
-  warp_select<KIND, CM>(mine, out);
-  return mx;
 }
 
 template <int KIND, int CM>
@@ -723,104 +756,254 @@ __device__ __forceinline__ void unpack_cand(const PackedCand<CM>& p, const NodeI
   c.key = (tkey << 8) | (p.fb & 255u);
 }
 
+// Histogram of one feature over a node of at most kRegRows rows whose entries
+// are staged in the warp's shared memory (ebuf), the feature's bins already
+// gathered into b (lane l holds rows q * 32 + l).
+template <int KIND>
+__device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const uint32_t* ebuf,
+                                            const uint32_t (&b)[kRegRows / 32], uint32_t* hw) {
+  const int lane = threadIdx.x & 31;
+  hist_clear<KIND>(d, hw);
+  __syncwarp();
+  if (KIND == 0) {
+#pragma unroll
+    for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) {
+      const uint32_t r = q * 32 + lane;
+      if (r < len) {
+        const uint32_t e = ebuf[r];
+        atomicAdd(&hw[b[q] * d.C + ent_y(e) + (b[q] >> 3)], ent_w<0>(e));
+      }
+    }
+  } else {
+    uint32_t* hn = hw;
+    unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + hist_words_n(d.B));
+#pragma unroll
+    for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) {
+      const uint32_t r = q * 32 + lane;
+      if (r < len) {
+        const uint32_t e = ebuf[r];
+        const uint32_t w = ent_w<1>(e);
+        const long long yq = d.yreg[e >> 8];
+        atomicAdd(&hn[b[q] + (b[q] >> 3)], w);
+        atomicAdd(&hs[b[q] + (b[q] >> 3)], static_cast<unsigned long long>(static_cast<long long>(w) * yq));
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void gather_staged(const uint8_t* col, uint32_t len, const uint32_t* ebuf,
+                                              uint32_t (&b)[kRegRows / 32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) {
+    const uint32_t r = q * 32 + lane;
+    b[q] = r < len ? col[ebuf[r] >> 8] : 0u;
+  }
+}
+
 // ---------------------------------------------------------------- feature-band path
-// item = rank << 36 | slot << 22 | feature
+// The level's (larger node, draw slot) items are cut into groups: the items
+// of one node whose features fall in one band of columns.  Groups are sorted
+// by band, so the warps sweep the augmented matrix band by band and a band's
+// columns stay in L2 while its groups run; a group of a node of at most
+// kRegRows rows reads the node's row entries once for all of its features,
+// into the warp's shared memory.
+//   item  = rank << 36 | slot << 22 | feature      (items_u, per node by band)
+//   group = rank << 28 | first item << 14 | count-1 (items_s, by band)
 __device__ __forceinline__ uint64_t pack_item(uint32_t rank, uint32_t slot, uint32_t f) {
   return (static_cast<uint64_t>(rank) << 36) | (static_cast<uint64_t>(slot) << 22) | f;
 }
 
+__device__ __forceinline__ uint64_t pack_group(uint32_t rank, uint32_t first, uint32_t count) {
+  return (static_cast<uint64_t>(rank) << 28) | (static_cast<uint64_t>(first) << 14) | (count - 1u);
+}
+
+// most items in a group of a node with len rows
+__device__ __forceinline__ uint32_t group_cap(uint32_t len) {
+  return len <= kRegRows ? (1u << 14) : max(1u, kGroupWork / len);
+}
+
+// Exclusive scan of a warp's per-band counters in place; returns the total.
+__device__ __forceinline__ uint32_t warp_scan_bands(uint32_t* cnt, int nbands, int lane) {
+  const int bpl = (nbands + 31) >> 5;
+  uint32_t sum = 0;
+  for (int q = 0; q < bpl; ++q) {
+    const int b = lane * bpl + q;
+    if (b < nbands) sum += cnt[b];
+  }
+  uint32_t run = warp_excl_scan_u32(sum, lane);
+  const uint32_t total = __shfl_sync(kFull, run + sum, 31);
+  for (int q = 0; q < bpl; ++q) {
+    const int b = lane * bpl + q;
+    if (b < nbands) {
+      const uint32_t c = cnt[b];
+      cnt[b] = run;
+      run += c;
+    }
+  }
+  __syncwarp();
+  return total;
+}
+
+// Per larger node (one warp): cache its totals, draw its mtry features,
+// write its items ordered by band and count its groups per band.
 template <int KIND, int CM>
 __global__ void __launch_bounds__(256) k_plan_gen(Dev d, int level) {
   __shared__ uint32_t sband[kMaxBands];
+  __shared__ uint32_t wcnt[8][kMaxBands];
   const uint32_t nbig = d.work[level];
   if (!band_path(d, nbig)) return;
   for (int b = threadIdx.x; b < d.nbands; b += blockDim.x) sband[b] = 0u;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* cnt = wcnt[warp];
+  const uint32_t bw = static_cast<uint32_t>(d.band_w);
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
     const uint32_t k = d.big[rank];
-    if (lane == 0) {  // the node's totals, read once here instead of by each of its items
+    uint32_t len = 0;
+    if (lane == 0) {  // the node's totals, read once here instead of by each of its groups
       NodeInfo<CM> nd;
       load_node<KIND, CM>(d, k, level, nd);
       reinterpret_cast<NodeInfo<CM>*>(d.ninfo)[rank] = nd;
+      len = nd.len;
     }
+    len = __shfl_sync(kFull, len, 0);
+    for (int b = lane; b < d.nbands; b += 32) cnt[b] = 0u;
+    __syncwarp();
     Perm P;
     node_perm(d, k, P);
+    for (int s = lane; s < d.mtry; s += 32) atomicAdd(&cnt[perm_apply(P, static_cast<uint32_t>(s)) / bw], 1u);
+    __syncwarp();
+    const uint32_t gc = group_cap(len);
+    for (int b = lane; b < d.nbands; b += 32)
+      if (cnt[b]) atomicAdd(&sband[b], (cnt[b] + gc - 1) / gc);
+    __syncwarp();
+    warp_scan_bands(cnt, d.nbands, lane);
+    uint64_t* out = d.items_u + static_cast<uint64_t>(rank) * d.mtry;
     for (int s = lane; s < d.mtry; s += 32) {
       const uint32_t f = perm_apply(P, static_cast<uint32_t>(s));
-      d.items_u[static_cast<uint64_t>(rank) * d.mtry + s] = pack_item(rank, static_cast<uint32_t>(s), f);
-      atomicAdd(&sband[f / static_cast<uint32_t>(d.band_w)], 1u);
+      out[atomicAdd(&cnt[f / bw], 1u)] = pack_item(rank, static_cast<uint32_t>(s), f);
     }
+    __syncwarp();
   }
   __syncthreads();
   for (int b = threadIdx.x; b < d.nbands; b += blockDim.x)
     if (sband[b]) atomicAdd(&d.band_cnt[b], sband[b]);
 }
 
-// exclusive scan of the band counts into band cursors (one block)
+// exclusive scan of the per-band group counts into band cursors, and the
+// total (one warp)
 __global__ void k_plan_scan(Dev d, int level) {
   if (!band_path(d, d.work[level])) return;
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int b = 0; b < d.nbands; ++b) {
-      const uint32_t c = d.band_cnt[b];
-      d.band_cnt[b] = run;
-      run += c;
-    }
-  }
+  const uint32_t total = warp_scan_bands(d.band_cnt, d.nbands, threadIdx.x & 31);
+  if (threadIdx.x == 0) d.band_cnt[kMaxBands] = total;
 }
 
+// Per larger node (one warp): its groups, placed in their bands.
+template <int KIND, int CM>
 __global__ void __launch_bounds__(256) k_plan_scatter(Dev d, int level) {
+  __shared__ uint32_t wcnt[8][kMaxBands];
   const uint32_t nbig = d.work[level];
   if (!band_path(d, nbig)) return;
-  const uint64_t total = static_cast<uint64_t>(nbig) * d.mtry;
-  const int lane = threadIdx.x & 31;
-  for (uint64_t base = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ull; base < total;
-       base += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-    const uint64_t i = base + lane;
-    const bool v = i < total;
-    const uint64_t it = v ? d.items_u[i] : 0ull;
-    const uint32_t band = v ? static_cast<uint32_t>(it & 0x3FFFFFu) / static_cast<uint32_t>(d.band_w) : 0xFFFFFFFFu;
-    // one atomic per distinct band in the warp
-    const unsigned grp = __match_any_sync(kFull, band);
-    const int leader = __ffs(grp) - 1;
-    uint32_t pos = 0;
-    if (v && lane == leader) pos = atomicAdd(&d.band_cnt[band], static_cast<uint32_t>(__popc(grp)));
-    pos = __shfl_sync(kFull, pos, leader);
-    if (v) d.items_s[pos + __popc(grp & lanemask_lt())] = it;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* cnt = wcnt[warp];
+  const uint32_t bw = static_cast<uint32_t>(d.band_w);
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int bpl = (d.nbands + 31) >> 5;
+  for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
+    const uint32_t len = reinterpret_cast<const NodeInfo<CM>*>(d.ninfo)[rank].len;
+    const uint64_t* items = d.items_u + static_cast<uint64_t>(rank) * d.mtry;
+    for (int b = lane; b < d.nbands; b += 32) cnt[b] = 0u;
+    __syncwarp();
+    for (int s = lane; s < d.mtry; s += 32)
+      atomicAdd(&cnt[static_cast<uint32_t>(items[s] & 0x3FFFFFu) / bw], 1u);
+    __syncwarp();
+    // lane-owned bands: count, then node-local start (the items are in band order)
+    uint32_t c[8];  // bpl <= 8 (at most 256 bands)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int b = lane * bpl + q;
+      c[q] = (q < bpl && b < d.nbands) ? cnt[b] : 0u;
+    }
+    __syncwarp();
+    warp_scan_bands(cnt, d.nbands, lane);
+    const uint32_t gc = group_cap(len);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int b = lane * bpl + q;
+      if (q >= bpl || b >= d.nbands || c[q] == 0u) continue;
+      const uint32_t first = cnt[b], n = c[q], ng = (n + gc - 1) / gc;
+      const uint32_t pos = atomicAdd(&d.band_cnt[b], ng);
+      for (uint32_t g = 0; g < ng; ++g)
+        d.items_s[pos + g] = pack_group(rank, first + g * gc, min(gc, n - g * gc));
+    }
+    __syncwarp();
   }
 }
 
-// one warp per band-sorted item: the feature's exact best candidate, packed
+// one warp per group: each feature's exact best candidate, packed
 template <int KIND, int CM>
 __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band(Dev d, int level) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
+  uint32_t* ebuf = hw + hist_smem_per_warp(d.kind, d.C, d.B) / 4;
   const uint32_t nbig = d.work[level];
   if (!band_path(d, nbig)) return;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
-  const uint64_t total = static_cast<uint64_t>(nbig) * d.mtry;
+  const uint32_t total = d.band_cnt[kMaxBands];
   unsigned long long bytes = 0;
-  for (uint64_t i = gwarp; i < total; i += nwarps) {
-    const uint64_t it = d.items_s[i];
-    const uint32_t rank = static_cast<uint32_t>(it >> 36);
-    const uint32_t slot = static_cast<uint32_t>(it >> 22) & 0x3FFFu;
-    const uint32_t f = static_cast<uint32_t>(it & 0x3FFFFFu);
-    NodeInfo<CM> nd;
-    nd = reinterpret_cast<const NodeInfo<CM>*>(d.ninfo)[rank];
-    build_hist<KIND>(d, nd.base, nd.len, rows_in, column(d, f), hw);
-    Cand<CM> c;
-    scan_hist<KIND, CM>(d, nd, hw, true, static_cast<int>(f), 0u, c);
-    if (lane == 0)
-      reinterpret_cast<PackedCand<CM>*>(d.fbest)[static_cast<uint64_t>(rank) * d.mtry + slot] = pack_cand<KIND, CM>(c);
-    // algorithmic bytes: one row entry and one bin per row (+ the target for
-    // regression), and the packed candidate
-    bytes += static_cast<unsigned long long>(nd.len) * (KIND ? 13ull : 5ull) + sizeof(PackedCand<CM>);
+  for (uint32_t g = gwarp; g < total; g += nwarps) {
+    const uint64_t gr = d.items_s[g];
+    const uint32_t rank = static_cast<uint32_t>(gr >> 28);
+    const uint32_t first = static_cast<uint32_t>(gr >> 14) & 0x3FFFu;
+    const uint32_t count = static_cast<uint32_t>(gr & 0x3FFFu) + 1u;
+    const NodeInfo<CM> nd = reinterpret_cast<const NodeInfo<CM>*>(d.ninfo)[rank];
+    const uint64_t* items = d.items_u + static_cast<uint64_t>(rank) * d.mtry + first;
+    PackedCand<CM>* out = reinterpret_cast<PackedCand<CM>*>(d.fbest) + static_cast<uint64_t>(rank) * d.mtry;
+    // A node of at most kRegRows rows: its entries are read once, into the
+    // warp's shared-memory buffer, for all the group's features, and the
+    // next feature's bins are gathered while this one's are counted and
+    // scanned.  Larger nodes stream their entries per feature.
+    const bool staged = nd.len <= kRegRows;
+    if (staged) {
+      for (uint32_t r = lane; r < nd.len; r += 32) ebuf[r] = rows_in[nd.base + r];
+      __syncwarp();
+    }
+    uint64_t chunk = items[lane < count ? lane : 0u];  // items j..j+31 of the group, one per lane
+    uint32_t bn[kRegRows / 32];
+    if (staged) gather_staged(column(d, static_cast<uint32_t>(__shfl_sync(kFull, chunk, 0) & 0x3FFFFFu)), nd.len,
+                              ebuf, bn);
+    for (uint32_t j = 0; j < count; ++j) {
+      const uint64_t it = __shfl_sync(kFull, chunk, j & 31);
+      const uint32_t f = static_cast<uint32_t>(it & 0x3FFFFFu);
+      if (j + 1 < count && ((j + 1) & 31) == 0) chunk = items[j + 1 + lane < count ? j + 1 + lane : j + 1];
+      if (staged) {
+        uint32_t b[kRegRows / 32];
+#pragma unroll
+        for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) b[q] = bn[q];
+        if (j + 1 < count)
+          gather_staged(column(d, static_cast<uint32_t>(__shfl_sync(kFull, chunk, (j + 1) & 31) & 0x3FFFFFu)),
+                        nd.len, ebuf, bn);
+        hist_staged<KIND>(d, nd.len, ebuf, b, hw);
+      } else {
+        build_hist<KIND>(d, nd.base, nd.len, rows_in, column(d, f), hw);
+      }
+      Cand<CM> c;
+      scan_hist<KIND, CM>(d, nd, hw, true, static_cast<int>(f), 0u, c);
+      if (lane == 0) out[static_cast<uint32_t>(it >> 22) & 0x3FFFu] = pack_cand<KIND, CM>(c);
+    }
+    __syncwarp();  // the entry buffer is reused by the next group
+    // algorithmic bytes (the method's per-level figure): one bin per row and
+    // feature, and the node's row state once (entry read and rewritten, weight
+    // and label, or the 8-byte target for regression)
+    bytes += static_cast<unsigned long long>(nd.len) * (count + (first == 0u ? (KIND ? kRowStateReg : kRowStateClass) : 0u));
   }
   if (lane == 0 && bytes) atomicAdd(&d.counters[2], bytes);
 }
@@ -959,10 +1142,10 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_
   k_split_small<KIND, CM><<<grid_small, 256, 0, st2>>>(d, level);
   cudaEventRecord(join, st2);
   if (d.band_w > 0) {
-    cudaMemsetAsync(d.band_cnt, 0, kMaxBands * sizeof(uint32_t), st);
+    cudaMemsetAsync(d.band_cnt, 0, (kMaxBands + 1) * sizeof(uint32_t), st);
     k_plan_gen<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
     k_plan_scan<<<1, 32, 0, st>>>(d, level);
-    k_plan_scatter<<<grid_small, 256, 0, st>>>(d, level);
+    k_plan_scatter<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   }
   // the histogram kernel of the level (one of the two does the work)
   cudaEventRecord(hist_start, st);

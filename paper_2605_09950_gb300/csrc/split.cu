@@ -35,6 +35,9 @@
 #ifndef BORUTA_SMALL_MINB
 #define BORUTA_SMALL_MINB 4
 #endif
+#ifndef BORUTA_STREAM_BATCH
+#define BORUTA_STREAM_BATCH 8  // rows per lane per pass of a streamed histogram
+#endif
 #ifndef BORUTA_ITEMS_MINB
 #define BORUTA_ITEMS_MINB 3
 #endif
@@ -546,13 +549,13 @@ __device__ __forceinline__ void hist_add(const Dev& d, uint32_t r0, uint32_t len
 }
 
 // Warp-private histogram of one feature over a node's rows.  Rows are
-// gathered 8 per lane per pass so that 8 independent loads per lane are in
-// flight.
+// gathered BORUTA_STREAM_BATCH per lane per pass so that as many independent
+// loads per lane are in flight.
 template <int KIND>
 __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint32_t* rows, const uint8_t* col,
                            uint32_t* hw) {
   const int lane = threadIdx.x & 31;
-  constexpr int kBatch = 8;
+  constexpr int kBatch = BORUTA_STREAM_BATCH;
   hist_clear<KIND>(d, hw);
   uint32_t e[kBatch];
 #pragma unroll
@@ -574,32 +577,59 @@ __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint3
   __syncwarp();
 }
 
-// Scan of a built histogram.  Lane l owns bins [l*bpl, (l+1)*bpl).
-// Returns the warp's best float score (-1 if no valid candidate); with
-// `exact`, also returns in `out` the exact best among the candidates within
-// the screen window.  An empty bin repeats the partition of the nearest
-// non-empty bin below it, which has the lower bin and wins the tie, so empty
-// bins are skipped: a lane visits only its non-empty bins (a bit mask), and
-// only a lane whose own best float score is inside the window revisits them
-// for the exact comparison.
+// Float pre-screen of a built histogram.  Lane l owns bins [l*bpl,
+// (l+1)*bpl).  An empty bin repeats the partition of the nearest non-empty
+// bin below it, which has the lower bin and wins the tie, so empty bins are
+// skipped: a lane visits only its non-empty bins (a bit mask), and keeps its
+// best float score with that bin's left totals, and its second-best score.
+template <int CM>
+struct Screen {
+  uint32_t pre[CM];  // left totals before the lane's bins (regression: count)
+  long long ps;      // regression: target sum before the lane's bins
+  uint32_t mask;     // non-empty bins of the lane that can be thresholds
+  float lmax, s2;    // best and second-best float score (-1: none)
+  int bbest;         // bin of lmax
+  uint32_t nLb;      // left count at bbest
+  uint32_t cb[CM];   // class: left class counts at bbest
+  long long SLb;     // regression: left target sum at bbest
+};
+
+template <int CM>
+__device__ __forceinline__ void screen_keep(Screen<CM>& S, float sc, int bb, uint32_t nL, const uint32_t* cum,
+                                            long long SL) {
+  if (sc > S.lmax) {
+    S.s2 = S.lmax;
+    S.lmax = sc;
+    S.bbest = bb;
+    S.nLb = nL;
+#pragma unroll
+    for (int k = 0; k < CM; ++k) S.cb[k] = cum[k];
+    S.SLb = SL;
+  } else if (sc > S.s2) {
+    S.s2 = sc;
+  }
+}
+
 template <int KIND, int CM>
-__device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, bool exact, int feat,
-                           uint32_t tkey, Cand<CM>& out) {
+__device__ __forceinline__ void scan_screen(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, Screen<CM>& S) {
   const int lane = threadIdx.x & 31;
   const int C = d.C, B = d.B;
   const int bpl = (B + 31) >> 5;  // bins per lane (<= 8)
   const int b0 = lane * bpl;
-  const uint32_t* hn = hw;
-  const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(hw + hist_words_n(B));
-  Cand<CM> mine;
-  mine.valid = false;
-  out.valid = false;
-  float lmax = -1.0f;
-  uint32_t mask = 0;  // non-empty bins of the lane that can be thresholds
+  S.mask = 0u;
+  S.lmax = -1.0f;
+  S.s2 = -1.0f;
+  S.bbest = 0;
+  S.nLb = 0u;
+  S.SLb = 0;
+  S.ps = 0;
   if (KIND == 0) {
-    uint32_t pre[CM], cum[CM];
+    uint32_t cum[CM];
 #pragma unroll
-    for (int k = 0; k < CM; ++k) pre[k] = 0u;
+    for (int k = 0; k < CM; ++k) {
+      S.pre[k] = 0u;
+      S.cb[k] = 0u;
+    }
     for (int q = 0; q < bpl; ++q) {
       const int bb = b0 + q;
       if (bb < B) {
@@ -608,18 +638,18 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
         for (int k = 0; k < CM; ++k)
           if (k < C) {
             const uint32_t h = hw[bb * C + k + (bb >> 3)];
-            pre[k] += h;
+            S.pre[k] += h;
             wb += h;
           }
-        if (wb > 0u && bb < B - 1) mask |= 1u << q;
+        if (wb > 0u && bb < B - 1) S.mask |= 1u << q;
       }
     }
 #pragma unroll
     for (int k = 0; k < CM; ++k) {
-      pre[k] = warp_excl_scan_u32(pre[k], lane);
-      cum[k] = pre[k];
+      S.pre[k] = warp_excl_scan_u32(S.pre[k], lane);
+      cum[k] = S.pre[k];
     }
-    for (uint32_t m = mask; m; m &= m - 1) {
+    for (uint32_t m = S.mask; m; m &= m - 1) {
       const int bb = b0 + __ffs(m) - 1;
       uint32_t nL = 0;
 #pragma unroll
@@ -628,15 +658,53 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
           cum[k] += hw[bb * C + k + (bb >> 3)];
           nL += cum[k];
         }
-      if (nL < nd.n) lmax = fmaxf(lmax, score_class_f<CM>(cum, nd.cp, C, nL, nd.n));
+      if (nL < nd.n) screen_keep<CM>(S, score_class_f<CM>(cum, nd.cp, C, nL, nd.n), bb, nL, cum, 0);
     }
-    const float mx = warp_max_f(lmax);
-    if (!exact || mx < 0.0f) return mx;
-    const float thr = screen(mx);
-    if (lmax >= thr) {
+  } else {
+    const uint32_t* hn = hw;
+    const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(hw + hist_words_n(B));
+    uint32_t tn = 0;
+    long long ts = 0;
 #pragma unroll
-      for (int k = 0; k < CM; ++k) cum[k] = pre[k];
-      for (uint32_t m = mask; m; m &= m - 1) {
+    for (int k = 0; k < CM; ++k) S.cb[k] = 0u;
+    for (int q = 0; q < bpl; ++q) {
+      const int bb = b0 + q;
+      if (bb < B) {
+        const uint32_t h = hn[bb + (bb >> 3)];
+        tn += h;
+        ts += static_cast<long long>(hs[bb + (bb >> 3)]);
+        if (h > 0u && bb < B - 1) S.mask |= 1u << q;
+      }
+    }
+    S.pre[0] = warp_excl_scan_u32(tn, lane);
+    S.ps = warp_excl_scan_i64(ts, lane);
+    uint32_t cn = S.pre[0];
+    long long cs = S.ps;
+    for (uint32_t m = S.mask; m; m &= m - 1) {
+      const int bb = b0 + __ffs(m) - 1;
+      cn += hn[bb + (bb >> 3)];
+      cs += static_cast<long long>(hs[bb + (bb >> 3)]);
+      if (cn < nd.n) screen_keep<CM>(S, score_reg_f(cs, nd.SP, cn, nd.n), bb, cn, S.cb, cs);
+    }
+  }
+}
+
+// Exact best among the candidates whose float score is at least thr (all
+// lanes; only a lane whose own best is inside the window revisits its bins).
+template <int KIND, int CM>
+__device__ void scan_exact(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, const Screen<CM>& S, float thr,
+                           int feat, uint32_t tkey, Cand<CM>& out) {
+  const int lane = threadIdx.x & 31;
+  const int C = d.C, B = d.B;
+  const int b0 = lane * ((B + 31) >> 5);
+  Cand<CM> mine;
+  mine.valid = false;
+  if (S.lmax >= thr) {
+    if (KIND == 0) {
+      uint32_t cum[CM];
+#pragma unroll
+      for (int k = 0; k < CM; ++k) cum[k] = S.pre[k];
+      for (uint32_t m = S.mask; m; m &= m - 1) {
         const int bb = b0 + __ffs(m) - 1;
         uint32_t nL = 0;
 #pragma unroll
@@ -654,38 +722,12 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
           if (better(c, mine)) mine = c;
         }
       }
-    }
-    warp_select<KIND, CM>(mine, out);
-    return mx;
-  } else {
-    uint32_t tn = 0;
-    long long ts = 0;
-    for (int q = 0; q < bpl; ++q) {
-      const int bb = b0 + q;
-      if (bb < B) {
-        const uint32_t h = hn[bb + (bb >> 3)];
-        tn += h;
-        ts += static_cast<long long>(hs[bb + (bb >> 3)]);
-        if (h > 0u && bb < B - 1) mask |= 1u << q;
-      }
-    }
-    const uint32_t pn = warp_excl_scan_u32(tn, lane);
-    const long long ps = warp_excl_scan_i64(ts, lane);
-    uint32_t cn = pn;
-    long long cs = ps;
-    for (uint32_t m = mask; m; m &= m - 1) {
-      const int bb = b0 + __ffs(m) - 1;
-      cn += hn[bb + (bb >> 3)];
-      cs += static_cast<long long>(hs[bb + (bb >> 3)]);
-      if (cn < nd.n) lmax = fmaxf(lmax, score_reg_f(cs, nd.SP, cn, nd.n));
-    }
-    const float mx = warp_max_f(lmax);
-    if (!exact || mx < 0.0f) return mx;
-    const float thr = screen(mx);
-    if (lmax >= thr) {
-      cn = pn;
-      cs = ps;
-      for (uint32_t m = mask; m; m &= m - 1) {
+    } else {
+      const uint32_t* hn = hw;
+      const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(hw + hist_words_n(B));
+      uint32_t cn = S.pre[0];
+      long long cs = S.ps;
+      for (uint32_t m = S.mask; m; m &= m - 1) {
         const int bb = b0 + __ffs(m) - 1;
         cn += hn[bb + (bb >> 3)];
         cs += static_cast<long long>(hs[bb + (bb >> 3)]);
@@ -699,9 +741,24 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
         }
       }
     }
-    warp_select<KIND, CM>(mine, out);
-    return mx;
   }
+  warp_select<KIND, CM>(mine, out);
+}
+
+// Scan of a built histogram: returns the warp's best float score (-1 if no
+// valid candidate) and in `out` the feature's exact best candidate (all
+// lanes).  The float screen keeps every candidate whose exact score is the
+// maximum, and only those are compared exactly.
+template <int KIND, int CM>
+__device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, bool exact, int feat,
+                           uint32_t tkey, Cand<CM>& out) {
+  Screen<CM> S;
+  scan_screen<KIND, CM>(d, nd, hw, S);
+  const float mx = warp_max_f(S.lmax);
+  out.valid = false;
+  if (!exact || mx < 0.0f) return mx;
+  scan_exact<KIND, CM>(d, nd, hw, S, screen(mx), feat, tkey, out);
+  return mx;
 }
 
 template <int KIND, int CM>
@@ -756,6 +813,50 @@ __device__ __forceinline__ void unpack_cand(const PackedCand<CM>& p, const NodeI
   c.key = (tkey << 8) | (p.fb & 255u);
 }
 
+// A feature's exact best candidate, packed, from its built histogram.  When
+// a single candidate lies inside the float screen window it is the exact
+// best and is packed as is; otherwise the candidates inside the window are
+// compared exactly.
+template <int KIND, int CM>
+__device__ void scan_pack(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, uint32_t f, PackedCand<CM>* dst) {
+  const int lane = threadIdx.x & 31;
+  Screen<CM> S;
+  scan_screen<KIND, CM>(d, nd, hw, S);
+  const float mx = warp_max_f(S.lmax);
+  if (mx < 0.0f) {
+    if (lane == 0) {
+      PackedCand<CM> p;
+      p.fb = kLeaf;
+      p.nL = 0u;
+#pragma unroll
+      for (int k = 0; k < (CM > 1 ? CM : 2); ++k) p.cL[k] = 0u;
+      *dst = p;
+    }
+    return;
+  }
+  const float thr = screen(mx);
+  const uint32_t mine = (S.lmax >= thr ? 1u : 0u) + (S.s2 >= thr ? 1u : 0u);
+  if (__reduce_add_sync(kFull, mine) == 1u) {
+    if (mine) {
+      PackedCand<CM> p;
+      p.fb = (f << 8) | static_cast<uint32_t>(S.bbest);
+      p.nL = S.nLb;
+      if (KIND == 1) {
+        p.cL[0] = static_cast<uint32_t>(static_cast<unsigned long long>(S.SLb));
+        p.cL[1] = static_cast<uint32_t>(static_cast<unsigned long long>(S.SLb) >> 32);
+      } else {
+#pragma unroll
+        for (int k = 0; k < CM; ++k) p.cL[k] = S.cb[k];
+      }
+      *dst = p;
+    }
+  } else {
+    Cand<CM> c;
+    scan_exact<KIND, CM>(d, nd, hw, S, thr, static_cast<int>(f), 0u, c);
+    if (lane == 0) *dst = pack_cand<KIND, CM>(c);
+  }
+}
+
 // Histogram of one feature over a node of at most kRegRows rows whose entries
 // are staged in the warp's shared memory (ebuf), the feature's bins already
 // gathered into b (lane l holds rows q * 32 + l).
@@ -800,6 +901,18 @@ __device__ __forceinline__ void gather_staged(const uint8_t* col, uint32_t len, 
     const uint32_t r = q * 32 + lane;
     b[q] = r < len ? col[ebuf[r] >> 8] : 0u;
   }
+}
+
+// float score of a packed candidate (-1 for a feature without a valid split)
+template <int KIND, int CM>
+__device__ __forceinline__ float packed_score_f(const PackedCand<CM>& p, const NodeInfo<CM>& nd, int C) {
+  if (p.fb == kLeaf) return -1.0f;
+  if (KIND == 1) {
+    const long long SL = static_cast<long long>(static_cast<unsigned long long>(p.cL[0]) |
+                                                (static_cast<unsigned long long>(p.cL[1]) << 32));
+    return score_reg_f(SL, nd.SP, p.nL, nd.n);
+  }
+  return score_class_f<CM>(p.cL, nd.cp, C, p.nL, nd.n);
 }
 
 // ---------------------------------------------------------------- feature-band path
@@ -995,9 +1108,7 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
       } else {
         build_hist<KIND>(d, nd.base, nd.len, rows_in, column(d, f), hw);
       }
-      Cand<CM> c;
-      scan_hist<KIND, CM>(d, nd, hw, true, static_cast<int>(f), 0u, c);
-      if (lane == 0) out[static_cast<uint32_t>(it >> 22) & 0x3FFFu] = pack_cand<KIND, CM>(c);
+      scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu));
     }
     __syncwarp();  // the entry buffer is reused by the next group
     // algorithmic bytes (the method's per-level figure): one bin per row and
@@ -1025,17 +1136,26 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize_band(Dev d,
     NodeInfo<CM> nd;
     load_node<KIND, CM>(d, k, level, nd);
     const PackedCand<CM>* pc = reinterpret_cast<const PackedCand<CM>*>(d.fbest) + static_cast<uint64_t>(rank) * d.mtry;
+    // float screen over the per-feature bests, then the exact argmax among
+    // those inside the window
+    float lmax = -1.0f;
+    for (int s = lane; s < d.mtry; s += 32) lmax = fmaxf(lmax, packed_score_f<KIND, CM>(pc[s], nd, d.C));
+    const float mx = warp_max_f(lmax);
+    const float thr = screen(mx);
     Cand<CM> best;
     best.valid = false;
-    for (int s0 = 0; s0 < d.mtry; s0 += 32) {
+    for (int s0 = 0; mx >= 0.0f && s0 < d.mtry; s0 += 32) {
       const int s = s0 + lane;
       Cand<CM> mine;
       mine.valid = false;
       if (s < d.mtry) {
         const PackedCand<CM> p = pc[s];
-        const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(s) : (p.fb >> 8);
-        unpack_cand<KIND, CM>(p, nd, d.C, tkey, mine);
+        if (packed_score_f<KIND, CM>(p, nd, d.C) >= thr) {
+          const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(s) : (p.fb >> 8);
+          unpack_cand<KIND, CM>(p, nd, d.C, tkey, mine);
+        }
       }
+      if (__ballot_sync(kFull, mine.valid) == 0u) continue;
       Cand<CM> c;
       warp_select<KIND, CM>(mine, c);
       if (better(c, best)) best = c;

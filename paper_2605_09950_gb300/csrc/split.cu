@@ -353,43 +353,76 @@ __device__ uint32_t warp_partition(const Dev& d, int64_t base, uint32_t len, uin
 }
 
 // ============================================================ small nodes
+// Bit planes of a small node's rows (one row per lane): the valid lanes, the
+// five bits of each row's weight and, per class, the lanes of that class.
+template <int CM>
+struct SmallPlanes {
+  unsigned valid;
+  unsigned w[5];
+  unsigned y[CM];
+};
+
 // Best split of one feature for a node of <= 32 rows, one row per lane.
+// Classification: the lanes whose bin is <= this lane's bin come from eight
+// ballots over the bin bits (most significant first), and the left class
+// counts from population counts against the weight and class bit planes.
+// Regression: the left sums are accumulated over the rows by shuffles.
+// Updates the node's exact best (best) and best float score so far (bestf).
 template <int KIND, int CM>
 __device__ void small_feature(const NodeInfo<CM>& nd, int C, bool v, uint32_t b, uint32_t w, uint32_t y,
-                              long long yv, int feat, uint32_t tkey, Cand<CM>& out) {
+                              long long yv, const SmallPlanes<CM>& pl, int feat, uint32_t tkey, float& bestf,
+                              Cand<CM>& best) {
   uint32_t cl[CM];
 #pragma unroll
   for (int k = 0; k < CM; ++k) cl[k] = 0u;
   uint32_t nL = 0;
   long long SL = 0;
-  for (int j = 0; j < static_cast<int>(nd.len); ++j) {
-    const uint32_t bj = __shfl_sync(kFull, b, j), wj = __shfl_sync(kFull, w, j);
-    if (KIND == 1) {
+  unsigned same;
+  if (KIND == 0) {
+    unsigned lt = 0u, eq = pl.valid;
+#pragma unroll
+    for (int t = 7; t >= 0; --t) {
+      const unsigned bt = __ballot_sync(kFull, (b >> t) & 1u);
+      const bool one = (b >> t) & 1u;
+      lt |= one ? (eq & ~bt) : 0u;
+      eq &= one ? bt : ~bt;
+    }
+    const unsigned le = lt | eq;
+#pragma unroll
+    for (int k = 0; k < CM; ++k)
+      if (k < C) {
+        const unsigned m = le & pl.y[k];
+        uint32_t c = 0;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) c += static_cast<uint32_t>(__popc(m & pl.w[t])) << t;
+        cl[k] = c;
+        nL += c;
+      }
+    same = v ? eq : 0u;
+  } else {
+    for (int j = 0; j < static_cast<int>(nd.len); ++j) {
+      const uint32_t bj = __shfl_sync(kFull, b, j), wj = __shfl_sync(kFull, w, j);
       const long long yj = __shfl_sync(kFull, yv, j);
       if (bj <= b) {
         nL += wj;
         SL += static_cast<long long>(wj) * yj;
       }
-    } else {
-      const uint32_t yj = __shfl_sync(kFull, y, j);
-      if (bj <= b) {
-        nL += wj;
-#pragma unroll
-        for (int k = 0; k < CM; ++k) cl[k] += (yj == static_cast<uint32_t>(k)) ? wj : 0u;
-      }
     }
+    same = __match_any_sync(kFull, v ? b : 0xFFFFFFFFu);
   }
   // lanes holding the same bin propose the same partition: the lowest one speaks
-  const unsigned same = __match_any_sync(kFull, v ? b : 0xFFFFFFFFu);
   const bool ok = v && nL < nd.n && (__ffs(same) - 1) == (threadIdx.x & 31);
   float sf = -1.0f;
   if (ok) sf = KIND == 1 ? score_reg_f(SL, nd.SP, nL, nd.n) : score_class_f<CM>(cl, nd.cp, C, nL, nd.n);
   const float mx = warp_max_f(sf);
-  out.valid = false;
-  if (mx < 0.0f) return;
+  // a feature whose best float score is below the window of the node's best
+  // so far cannot hold the node's exact best
+  if (mx < 0.0f || mx < screen(bestf)) return;
+  const float thr = screen(fmaxf(mx, bestf));
+  bestf = fmaxf(mx, bestf);
   Cand<CM> mine;
   mine.valid = false;
-  if (ok && sf >= screen(mx)) {
+  if (ok && sf >= thr) {
     if (KIND == 1)
       make_reg<CM>(mine, SL, nd.SP, nL, nd.n);
     else
@@ -398,7 +431,9 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, bool v, uint32_t b,
     mine.bin = static_cast<int32_t>(b);
     mine.key = (tkey << 8) | b;
   }
-  warp_select<KIND, CM>(mine, out);
+  Cand<CM> c;
+  warp_select<KIND, CM>(mine, c);
+  if (better(c, best)) best = c;
 }
 
 // One thread per node of the level: leaves are marked, active nodes are
@@ -454,26 +489,29 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
     const uint32_t row = e >> 8, w = v ? ent_w<KIND>(e) : 0u;
     const uint32_t y = KIND == 0 ? ent_y(e) : 0u;
     const long long yv = (KIND == 1 && v) ? d.yreg[row] : 0ll;
+    SmallPlanes<CM> pl;
+    pl.valid = __ballot_sync(kFull, v);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) pl.w[t] = __ballot_sync(kFull, (w >> t) & 1u);
+#pragma unroll
+    for (int c = 0; c < CM; ++c) pl.y[c] = __ballot_sync(kFull, v && y == static_cast<uint32_t>(c));
     Cand<CM> best;
     best.valid = false;
+    float bestf = -1.0f;
     for (int r0 = 0; r0 < d.mtry; r0 += 32) {
       const int ns = min(32, d.mtry - r0);
       const uint32_t myf = lane < ns ? perm_apply(P, static_cast<uint32_t>(r0 + lane)) : 0u;
-      for (int j = 0; j < ns; j += 4) {
-        uint32_t fq[4], bq[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) fq[q] = __shfl_sync(kFull, myf, min(j + q, ns - 1));
-#pragma unroll
-        for (int q = 0; q < 4; ++q) bq[q] = (v && j + q < ns) ? column(d, fq[q])[row] : 0u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (j + q < ns) {
-            const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(r0 + j + q) : fq[q];
-            Cand<CM> c;
-            small_feature<KIND, CM>(nd, C, v, bq[q], w, y, yv, static_cast<int>(fq[q]), tkey, c);
-            if (better(c, best)) best = c;
-          }
-        }
+      // the next feature's bins are gathered while this one is scored (the
+      // shuffles run on all lanes, outside the per-lane conditions)
+      const uint32_t f0 = __shfl_sync(kFull, myf, 0);
+      uint32_t bn = v ? column(d, f0)[row] : 0u;
+      for (int j = 0; j < ns; ++j) {
+        const uint32_t f = __shfl_sync(kFull, myf, j);
+        const uint32_t fn = __shfl_sync(kFull, myf, min(j + 1, ns - 1));
+        const uint32_t b = bn;
+        if (j + 1 < ns) bn = v ? column(d, fn)[row] : 0u;
+        const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(r0 + j) : f;
+        small_feature<KIND, CM>(nd, C, v, b, w, y, yv, pl, static_cast<int>(f), tkey, bestf, best);
       }
     }
     uint32_t sp = 0;

@@ -286,6 +286,129 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+BATCH_METRIC = ("Boruta job-iterations/sec (64 independent classification jobs, N log-uniform in [500, 50000], "
+                "p log-uniform in [20, 5000], 2-4 classes, 200 trees, depth 10, OOB permutation importance)")
+
+
+def run_batch(args):
+    """The batched-jobs workload: one step = one Boruta iteration of all 64
+    jobs (boruta_batch_run, FP32 terms), against the plain form: the same
+    jobs one at a time, one session each, FP64 terms."""
+    # 64 job streams: more hardware work queues than the default 8 (read when
+    # the CUDA context is created, so before the first CUDA call)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import numpy as np
+    import torch
+
+    from paper_2605_09950_gb300 import boruta, build, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    t0 = time.perf_counter()
+    ws = synth.batch_jobs(n_jobs=args.jobs)
+    gen_s = time.perf_counter() - t0
+    jobs = [dict(X=torch.from_numpy(w.X).cuda(), y=torch.from_numpy(w.y).cuda(), N=w.N, **w.params()) for w in ws]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    opts = dict(precision=1, job=rank * 4096, stream=stream.cuda_stream)
+
+    B = boruta.Batch(jobs, **opts)  # warm-up on a throw-away batch
+    B.run(args.warmup)
+    B.close()
+    t1 = time.perf_counter()
+    B = boruta.Batch(jobs, **opts)
+    setup_s = time.perf_counter() - t1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_{os.getpid()}.csv")
+    proc, fh = start_clock_sampler(clk_path) if rank == 0 else (None, None)
+    # K iterations of every job, each job advancing as soon as its previous
+    # iteration completes (the jobs' inputs, ~1.5 GB with shadows, exceed L2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    e0.record(stream)
+    B.run(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    clocks = stop_clock_sampler(proc, fh, clk_path, local) if rank == 0 else None
+    batched = [B.read(j) for j in range(len(jobs))]
+    B.close()
+    value = world * len(jobs) * args.steps / (total_ms / 1000.0)
+
+    # the plain form: each job alone, FP64 terms, after one untimed iteration
+    plain_ms, same = 0.0, 0
+    for j, jb in enumerate(jobs):
+        params = ws[j].params()
+        nc = params.pop("n_classes")
+        S = boruta.Session(jb["X"], jb["y"], N=jb["N"], n_classes=nc, precision=0, job=rank * 4096 + j, **params)
+        fresh = S.read()
+        S.step()
+        S.write(fresh)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+        r = S.read()
+        S.close()
+        same += int((r["hits"] == batched[j]["hits"]).all() and (r["decision"] == batched[j]["decision"]).all())
+    plain = len(jobs) * args.steps / (plain_ms / 1000.0)
+
+    # end to end: host inputs, upload + K lockstep iterations + readback
+    host_jobs = [dict(X=w.X, y=w.y, N=w.N, **{**w.params(), "max_iter": args.steps}) for w in ws]
+    t2 = time.perf_counter()
+    boruta.boruta_fit_batch(host_jobs, host_inputs=1, precision=1, job=rank * 4096)
+    e2e_s = time.perf_counter() - t2
+    h2d = sum(int(w.X.nbytes + w.y.nbytes) for w in ws)
+    d2h = sum(int(w.p * 5 + 8 * args.steps * w.p + 8 * args.steps) for w in ws)
+    if rank == 0:
+        line = {
+            "metric": BATCH_METRIC, "value": value, "unit": "job-iterations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8+int64+f32",
+            "data": "synthetic",
+            "config": {"workload": "batch_64_jobs", "jobs": len(jobs), "sum_N_x_p": int(sum(w.N * w.p for w in ws)),
+                       "n_trees": 200, "max_depth": 10, "n_bins": 128, "importance": "permut_oob",
+                       "precision": "fp32 terms, exact sums",
+                       "l2": "inputs larger than L2 (X and shadows of 64 jobs ~1.5 GB); one 512 MiB flush before",
+                       "schedule": "boruta_batch_run: each job's next iteration enqueued when its last completes",
+                       "input_generation_s": gen_s, "batch_setup_s": setup_s},
+            "plain_form": {"value": plain, "unit": "job-iterations/s",
+                           "form": "one job at a time, one session each, fp64 terms",
+                           "jobs_with_identical_hits_and_decisions": same},
+            "batched_over_plain": value / plain,
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": len(jobs) * args.steps / e2e_s, "unit": "job-iterations/s",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "note": "boruta_fit_batch with host inputs: setup, upload, K iterations, readback"},
+            "gpu_launches": len(jobs) * (8 + 11 * 10) * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,9 +420,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
     ap.add_argument("--trees", type=int, default=None, help="fewer trees (profiling captures only)")
+    ap.add_argument("--workload", default="binary", choices=["binary", "batch"],
+                    help="binary: N=1e5 p=1000 (default); batch: 64 uneven jobs, batched vs plain form")
+    ap.add_argument("--jobs", type=int, default=64, help="batch workload: number of jobs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_gpu(args)
 

@@ -132,6 +132,31 @@ typedef struct {
 int boruta_fit_batch(int n_jobs, const boruta_job* jobs, const boruta_opts* opts, boruta_result* outs);
 
 /*
+ * Step-wise batch: boruta_fit_batch one lockstep iteration at a time.
+ *   boruta_batch_create   arguments as boruta_fit_batch; the jobs' X and y
+ *                         (device pointers) must stay valid until destroy
+ *   boruta_batch_step     one iteration of every unfinished job; on return
+ *                         the work is complete and opts->stream (if given)
+ *                         has waited for it; *running receives the number of
+ *                         jobs still unfinished (stepping with none left
+ *                         returns BORUTA_EINVAL)
+ *   boruta_batch_read     job j's state, as boruta_session_read
+ *   boruta_batch_destroy  frees every job's workspace and stream (NULL ok)
+ * Errors name the failing job; after an error in step the batch may only be
+ * read or destroyed. */
+typedef struct boruta_batch boruta_batch;
+
+int boruta_batch_create(int n_jobs, const boruta_job* jobs, const boruta_opts* opts, boruta_batch** out);
+int boruta_batch_step(boruta_batch* b, int32_t* running);
+/* Up to `iterations` more iterations of every unfinished job, each job
+ * advancing on its own as soon as its previous iteration completes (no
+ * lockstep barrier); same results as as many boruta_batch_step calls. */
+int boruta_batch_run(boruta_batch* b, int iterations, int32_t* running);
+int boruta_batch_read(boruta_batch* b, int job, int8_t* decision, int32_t* hits, double* imp_history,
+                      double* shadow_max, int32_t* t);
+void boruta_batch_destroy(boruta_batch* b);
+
+/*
  * Step-wise interface: the same computation one Boruta iteration at a time
  * (Alg. 1 loop body), for benchmarking, checkpoint/resume and inspection.
  * A session owns its device workspace; X and y must stay valid (device

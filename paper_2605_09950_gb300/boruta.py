@@ -23,7 +23,9 @@ STATUS = {0: "BORUTA_OK", -1: "BORUTA_EINVAL", -2: "BORUTA_EOVERFLOW", -3: "BORU
 
 # the exported symbols of include/boruta.h
 EXPORTS = [
-    "boruta_default_opts", "boruta_fit", "boruta_fit_batch", "boruta_session_create", "boruta_session_step",
+    "boruta_default_opts", "boruta_fit", "boruta_fit_batch", "boruta_batch_create", "boruta_batch_step",
+    "boruta_batch_run",
+    "boruta_batch_read", "boruta_batch_destroy", "boruta_session_create", "boruta_session_step",
     "boruta_session_read", "boruta_session_write", "boruta_session_dump",
     "boruta_session_kernel_stats", "boruta_session_destroy", "boruta_philox", "boruta_perm",
     "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_last_error",
@@ -88,6 +90,12 @@ def lib():
                                                   ct.POINTER(ct.c_double)]
         L.boruta_session_destroy.argtypes = [vp]
         L.boruta_session_destroy.restype = None
+        L.boruta_batch_create.argtypes = [ct.c_int, vp, vp, ct.POINTER(ct.c_void_p)]
+        L.boruta_batch_step.argtypes = [vp, ct.POINTER(ct.c_int32)]
+        L.boruta_batch_run.argtypes = [vp, ct.c_int, ct.POINTER(ct.c_int32)]
+        L.boruta_batch_read.argtypes = [vp, ct.c_int, vp, vp, vp, vp, ct.POINTER(ct.c_int32)]
+        L.boruta_batch_destroy.argtypes = [vp]
+        L.boruta_batch_destroy.restype = None
         L.boruta_philox.argtypes = [vp, vp, vp, i64, vp]
         L.boruta_perm.argtypes = [ct.c_uint64, ct.c_uint64, ct.c_uint32, ct.c_uint32, ct.c_uint32, vp, vp,
                                   i64, vp]
@@ -96,7 +104,8 @@ def lib():
         L.boruta_binom_tails_noalloc.argtypes = [vp, vp, vp, vp, i64, vp]
         L.boruta_last_error.restype = ct.c_char_p
         for name in EXPORTS:
-            if name not in ("boruta_default_opts", "boruta_session_destroy", "boruta_last_error"):
+            if name not in ("boruta_default_opts", "boruta_session_destroy", "boruta_batch_destroy",
+                            "boruta_last_error"):
                 getattr(L, name).restype = ct.c_int
         _lib = L
     return _lib
@@ -175,6 +184,63 @@ def boruta_fit_batch(jobs, **opts):
         out["iterations"] = res[j].iterations
     del keep
     return outs
+
+
+def _jobs_struct(jobs, host):
+    arr = (Job * max(1, len(jobs)))()
+    keep = []
+    for j, jb in enumerate(jobs):
+        xp, ld, N, p, yp, k = _xy(jb["X"], jb["y"], jb.get("N"), host)
+        keep.append(k)
+        arr[j] = Job(xp, ld, yp, N, p, jb["task"], jb["n_trees"], jb["max_depth"], jb.get("mtry", 0), jb["n_bins"],
+                     jb["max_iter"], jb.get("alpha", 0.01), jb.get("seed", 0), jb.get("n_classes", 0))
+    return arr, keep
+
+
+class Batch:
+    """Step-wise batch (boruta_batch_*): one lockstep iteration of every
+    unfinished job per step().  jobs as for boruta_fit_batch (device X/y)."""
+
+    def __init__(self, jobs, **opts):
+        self._arr, self._keep = _jobs_struct(jobs, 0)
+        self._opts = make_opts(**opts)
+        self._shapes = [(int(self._arr[j].p), int(jb["max_iter"])) for j, jb in enumerate(jobs)]
+        h = ct.c_void_p()
+        _check(lib().boruta_batch_create(len(jobs), self._arr, ct.byref(self._opts), ct.byref(h)))
+        self._h = h
+
+    def step(self) -> int:
+        running = ct.c_int32()
+        _check(lib().boruta_batch_step(self._h, ct.byref(running)))
+        return running.value
+
+    def run(self, iterations) -> int:
+        """Up to `iterations` more iterations per job, jobs advancing independently."""
+        running = ct.c_int32()
+        _check(lib().boruta_batch_run(self._h, iterations, ct.byref(running)))
+        return running.value
+
+    def read(self, j):
+        p, max_iter = self._shapes[j]
+        out = dict(decision=np.zeros(p, np.int8), hits=np.zeros(p, np.int32),
+                   imp_history=np.zeros((max_iter, p)), shadow_max=np.zeros(max_iter))
+        t = ct.c_int32()
+        _check(lib().boruta_batch_read(self._h, j, out["decision"].ctypes.data, out["hits"].ctypes.data,
+                                       out["imp_history"].ctypes.data, out["shadow_max"].ctypes.data,
+                                       ct.byref(t)))
+        out["iterations"] = t.value
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().boruta_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Session:

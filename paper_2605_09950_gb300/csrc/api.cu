@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "boruta.h"
@@ -130,7 +131,8 @@ static int check_args(const uint8_t* X, int64_t ld, const void* y, int64_t N, in
   if (n_trees < 1 || n_trees >= (1 << 20)) return fail(BORUTA_EINVAL, "n_trees = %d", n_trees);
   if (max_depth < 0 || max_depth > kMaxDepth) return fail(BORUTA_EINVAL, "max_depth = %d", max_depth);
   if (n_bins < 2 || n_bins > 256) return fail(BORUTA_EINVAL, "n_bins = %d outside [2, 256]", n_bins);
-  if (max_iter < 1 || max_iter > 126) return fail(BORUTA_EINVAL, "max_iter = %d outside [1, 126]", max_iter);
+  if (max_iter < 1 || max_iter > kMaxIterations)
+    return fail(BORUTA_EINVAL, "max_iter = %d outside [1, %d]", max_iter, kMaxIterations);
   if (!(alpha > 0.0)) return fail(BORUTA_EINVAL, "alpha must be positive");
   if (mtry < 0) return fail(BORUTA_EINVAL, "mtry = %d", mtry);
   if (o->n_classes < 0 || o->n_classes > kMaxClasses)
@@ -444,9 +446,18 @@ static int step_launch(boruta_session* s) {
   launch_bootstrap(d, s->tree_grid, st);
   CK_LAUNCH("bootstrap kernels");
   for (int level = 0; level < d.D; ++level) {
+    // grids sized to what the level can hold (every split kernel loops over
+    // its work, so any grid is correct): at most M * min(2^level, N) nodes, of
+    // which at most M * min(2^level, N/33) have more than 32 rows
+    const uint64_t width = 1ull << level;
+    const uint64_t nodes = static_cast<uint64_t>(d.M) * std::min<uint64_t>(width, static_cast<uint64_t>(d.N));
+    const uint64_t big = static_cast<uint64_t>(d.M) * std::min<uint64_t>(width, static_cast<uint64_t>(d.N) / 33);
+    const uint64_t groups = big * static_cast<uint64_t>(d.mtry);  // work items of the larger nodes, at most
+    const int gs = static_cast<int>(std::min<uint64_t>(s->small_grid, (nodes + 7) / 8));
+    const int gi = static_cast<int>(std::min<uint64_t>(s->split_grid, std::max<uint64_t>(1, (groups + 7) / 8)));
     CK(cudaEventRecord(s->ev[2 * level], st));
-    launch_split(d, level, s->small_grid, s->split_grid, s->split_smem, st, s->st2, s->fork, s->join,
-                 s->hev[2 * level], s->hev[2 * level + 1]);
+    launch_split(d, level, std::max(gs, 1), gi, s->split_smem, st, s->st2, s->fork, s->join, s->hev[2 * level],
+                 s->hev[2 * level + 1]);
     CK_LAUNCH("split kernels");
     CK(cudaEventRecord(s->ev[2 * level + 1], st));
     launch_children(d, level, st);
@@ -699,75 +710,193 @@ int boruta_fit(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p
   return rc;
 }
 
-int boruta_fit_batch(int n_jobs, const boruta_job* jobs, const boruta_opts* opts, boruta_result* outs) {
-  if (n_jobs < 0 || (n_jobs > 0 && (!jobs || !outs))) return fail(BORUTA_EINVAL, "bad batch arguments");
-  for (int j = 0; j < n_jobs; ++j)
-    if (!outs[j].decision || !outs[j].hits || !outs[j].imp_history || !outs[j].shadow_max)
-      return fail(BORUTA_EINVAL, "job %d: result buffers must not be NULL", j);
+}  // extern "C"
+
+struct boruta_batch {
+  std::vector<boruta_session*> ss;
+  std::vector<cudaEvent_t> done;  // per job, recorded after its iteration
+  cudaStream_t user = nullptr;
+  cudaEvent_t ready = nullptr;
+  bool failed = false;
+  ~boruta_batch() {
+    for (auto* s : ss) boruta_session_destroy(s);
+    for (cudaEvent_t e : done)
+      if (e) cudaEventDestroy(e);
+    if (ready) cudaEventDestroy(ready);
+  }
+};
+
+extern "C" {
+
+int boruta_batch_create(int n_jobs, const boruta_job* jobs, const boruta_opts* opts, boruta_batch** out) {
+  if (!out || n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(BORUTA_EINVAL, "bad batch arguments");
+  *out = nullptr;
   boruta_opts base;
   if (opts)
     base = *opts;
   else
     boruta_default_opts(&base);
-  cudaStream_t user = static_cast<cudaStream_t>(base.stream);
-  cudaEvent_t ready = nullptr;
-  CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-  CK(cudaEventRecord(ready, user));
-  std::vector<boruta_session*> ss(n_jobs, nullptr);
-  int rc = 0;
-  auto cleanup = [&]() {
-    std::string msg = g_error;
-    for (auto* s : ss) boruta_session_destroy(s);
-    cudaEventDestroy(ready);
+  auto* b = new boruta_batch();
+  b->user = static_cast<cudaStream_t>(base.stream);
+  b->ss.assign(n_jobs, nullptr);
+  b->done.assign(n_jobs, nullptr);
+  auto bail = [&](int rc) {
+    const std::string msg = g_error;
+    delete b;
     g_error = msg;
+    return rc;
   };
-  for (int j = 0; j < n_jobs && !rc; ++j) {
+  if (cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(b->ready, b->user) != cudaSuccess)
+    return bail(fail(BORUTA_ECUDA, "batch: event creation failed"));
+  for (int j = 0; j < n_jobs; ++j) {
     const boruta_job& J = jobs[j];
     boruta_opts o = base;
     o.job = base.job + static_cast<uint32_t>(j);
     o.n_classes = J.n_classes;
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamWaitEvent(st, ready, 0) != cudaSuccess) {
-      rc = fail(BORUTA_ECUDA, "job %d: stream creation failed", j);
+        cudaStreamWaitEvent(st, b->ready, 0) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done[j], cudaEventDisableTiming) != cudaSuccess) {
       if (st) cudaStreamDestroy(st);
-      break;
+      return bail(fail(BORUTA_ECUDA, "job %d: stream creation failed", j));
     }
     o.stream = st;
-    rc = boruta_session_create(J.X, J.ld, J.y, J.N, J.p, J.task, J.n_trees, J.max_depth, J.mtry, J.n_bins,
-                               J.max_iter, J.alpha, J.seed, &o, &ss[j]);
+    const int rc = boruta_session_create(J.X, J.ld, J.y, J.N, J.p, J.task, J.n_trees, J.max_depth, J.mtry,
+                                         J.n_bins, J.max_iter, J.alpha, J.seed, &o, &b->ss[j]);
     if (rc) {
       cudaStreamDestroy(st);
+      return bail(fail(rc, "job %d: %s", j, std::string(g_error).c_str()));
+    }
+    b->ss[j]->own_stream = true;
+  }
+  *out = b;
+  return 0;
+}
+
+// Lockstep: the unfinished jobs' iterations are enqueued one after another
+// (each on its own stream, after the caller's stream), then collected.
+int boruta_batch_step(boruta_batch* b, int32_t* running) {
+  if (!b) return fail(BORUTA_EINVAL, "batch is NULL");
+  if (b->failed) return fail(BORUTA_EINVAL, "batch: a previous step failed");
+  std::vector<int> active;
+  for (int j = 0; j < static_cast<int>(b->ss.size()); ++j)
+    if (!b->ss[j]->finished) active.push_back(j);
+  if (active.empty()) return fail(BORUTA_EINVAL, "batch: every job is finished");
+  int rc = 0;
+  if (cudaEventRecord(b->ready, b->user) != cudaSuccess) rc = fail(BORUTA_ECUDA, "batch: event record failed");
+  for (int j : active) {
+    if (rc) break;
+    if (cudaStreamWaitEvent(b->ss[j]->st, b->ready, 0) != cudaSuccess) {
+      rc = fail(BORUTA_ECUDA, "job %d: stream wait failed", j);
+      break;
+    }
+    if ((rc = step_launch(b->ss[j]))) {
       fail(rc, "job %d: %s", j, std::string(g_error).c_str());
       break;
     }
-    ss[j]->own_stream = true;
+    if (cudaEventRecord(b->done[j], b->ss[j]->st) != cudaSuccess ||
+        cudaStreamWaitEvent(b->user, b->done[j], 0) != cudaSuccess)
+      rc = fail(BORUTA_ECUDA, "job %d: event record failed", j);
   }
-  // lockstep: enqueue one iteration of every unfinished job, then collect them
-  while (!rc) {
-    std::vector<int> active;
-    for (int j = 0; j < n_jobs; ++j)
-      if (!ss[j]->finished) active.push_back(j);
-    if (active.empty()) break;
-    for (int j : active) {
-      if ((rc = step_launch(ss[j]))) {
-        fail(rc, "job %d: %s", j, std::string(g_error).c_str());
-        break;
+  for (int j : active) {
+    if (!b->ss[j]->pending_t) continue;
+    int32_t und = 0;
+    const int r = step_finish(b->ss[j], &und);
+    if (r && !rc) rc = fail(r, "job %d: %s", j, std::string(g_error).c_str());
+  }
+  if (rc) {
+    b->failed = true;
+    return rc;
+  }
+  int32_t left = 0;
+  for (auto* s : b->ss) left += s->finished ? 0 : 1;
+  if (running) *running = left;
+  return 0;
+}
+
+int boruta_batch_run(boruta_batch* b, int iterations, int32_t* running) {
+  if (!b) return fail(BORUTA_EINVAL, "batch is NULL");
+  if (b->failed) return fail(BORUTA_EINVAL, "batch: a previous step failed");
+  if (iterations < 0) return fail(BORUTA_EINVAL, "iterations = %d", iterations);
+  const int n = static_cast<int>(b->ss.size());
+  std::vector<int> left(n, 0);
+  int rc = 0;
+  if (cudaEventRecord(b->ready, b->user) != cudaSuccess) rc = fail(BORUTA_ECUDA, "batch: event record failed");
+  auto launch = [&](int j) {
+    if (cudaStreamWaitEvent(b->ss[j]->st, b->ready, 0) != cudaSuccess)
+      return fail(BORUTA_ECUDA, "job %d: stream wait failed", j);
+    int r = step_launch(b->ss[j]);
+    if (r) return fail(r, "job %d: %s", j, std::string(g_error).c_str());
+    if (cudaEventRecord(b->done[j], b->ss[j]->st) != cudaSuccess)
+      return fail(BORUTA_ECUDA, "job %d: event record failed", j);
+    return 0;
+  };
+  for (int j = 0; j < n && !rc; ++j) {
+    left[j] = b->ss[j]->finished ? 0 : iterations;
+    if (left[j] > 0) rc = launch(j);
+  }
+  // each job's next iteration is enqueued as soon as its last one completes
+  for (bool busy = true; busy;) {
+    busy = false;
+    for (int j = 0; j < n; ++j) {
+      if (!b->ss[j]->pending_t) continue;
+      const cudaError_t q = cudaEventQuery(b->done[j]);
+      if (q == cudaErrorNotReady && !rc) {
+        busy = true;
+        continue;
+      }
+      if (q != cudaSuccess && q != cudaErrorNotReady) cudaGetLastError();
+      int32_t und = 0;
+      const int r = step_finish(b->ss[j], &und);
+      if (r && !rc) rc = fail(r, "job %d: %s", j, std::string(g_error).c_str());
+      if (--left[j] > 0 && !b->ss[j]->finished && !rc) {
+        rc = launch(j);
+        busy = true;
       }
     }
-    for (int j : active) {
-      if (!ss[j]->pending_t) continue;
-      int32_t und = 0;
-      const int r = step_finish(ss[j], &und);
-      if (r && !rc) rc = fail(r, "job %d: %s", j, std::string(g_error).c_str());
-    }
+    if (busy) std::this_thread::yield();
   }
+  for (int j = 0; j < n; ++j)
+    if (cudaStreamWaitEvent(b->user, b->done[j], 0) != cudaSuccess && !rc)
+      rc = fail(BORUTA_ECUDA, "job %d: stream wait failed", j);
+  if (rc) {
+    b->failed = true;
+    return rc;
+  }
+  int32_t still = 0;
+  for (auto* s : b->ss) still += s->finished ? 0 : 1;
+  if (running) *running = still;
+  return 0;
+}
+
+int boruta_batch_read(boruta_batch* b, int job, int8_t* decision, int32_t* hits, double* imp_history,
+                      double* shadow_max, int32_t* t) {
+  if (!b || job < 0 || job >= static_cast<int>(b->ss.size())) return fail(BORUTA_EINVAL, "bad batch job index");
+  const int rc = boruta_session_read(b->ss[job], decision, hits, imp_history, shadow_max, t);
+  if (rc) return fail(rc, "job %d: %s", job, std::string(g_error).c_str());
+  return 0;
+}
+
+void boruta_batch_destroy(boruta_batch* b) { delete b; }
+
+int boruta_fit_batch(int n_jobs, const boruta_job* jobs, const boruta_opts* opts, boruta_result* outs) {
+  if (n_jobs < 0 || (n_jobs > 0 && (!jobs || !outs))) return fail(BORUTA_EINVAL, "bad batch arguments");
+  for (int j = 0; j < n_jobs; ++j)
+    if (!outs[j].decision || !outs[j].hits || !outs[j].imp_history || !outs[j].shadow_max)
+      return fail(BORUTA_EINVAL, "job %d: result buffers must not be NULL", j);
+  boruta_batch* b = nullptr;
+  int rc = boruta_batch_create(n_jobs, jobs, opts, &b);
+  int32_t running = n_jobs;
+  if (!rc && n_jobs > 0) rc = boruta_batch_run(b, kMaxIterations, &running);
   for (int j = 0; j < n_jobs && !rc; ++j) {
     int32_t t = 0;
-    rc = boruta_session_read(ss[j], outs[j].decision, outs[j].hits, outs[j].imp_history, outs[j].shadow_max, &t);
+    rc = boruta_batch_read(b, j, outs[j].decision, outs[j].hits, outs[j].imp_history, outs[j].shadow_max, &t);
     outs[j].iterations = t;
   }
-  cleanup();
+  const std::string msg = g_error;
+  boruta_batch_destroy(b);
+  g_error = msg;
   return rc;
 }
 

@@ -75,6 +75,7 @@ constexpr int kItemsPerNode = 16;  // work items (groups of draw slots) per larg
 constexpr int kMaxBands = 256;     // feature bands of the band-sorted path
 constexpr int64_t kBandBytes = 24ll << 20;  // column bytes per band (kept in L2 while in use)
 constexpr uint64_t kMaxItems = 64ull << 20;  // plan buffer capacity (items)
+constexpr int kMaxIterations = 126;          // max_iter limit (exact binomial tails in 128 bits)
 #ifndef BORUTA_STAGED_ROWS
 #define BORUTA_STAGED_ROWS 128
 #endif

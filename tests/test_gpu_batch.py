@@ -53,3 +53,38 @@ def test_batch_reports_the_failing_job():
     bad = dict(good, n_bins=1)
     with pytest.raises(boruta.BorutaError, match="job 1"):
         boruta.boruta_fit_batch([good, bad])
+
+
+def test_stepwise_batch_matches_fit_batch():
+    import torch
+
+    import __graft_entry__
+    from paper_2605_09950_gb300 import boruta
+
+    __graft_entry__.build()
+    ws = _jobs()[:4]
+    jobs = [dict(X=torch.from_numpy(w.X).cuda(), y=torch.from_numpy(w.y).cuda(), N=w.N, **w.params()) for w in ws]
+    want = boruta.boruta_fit_batch(jobs, job=7, precision=1)
+    B = boruta.Batch(jobs, job=7, precision=1)
+    steps, running = 0, len(jobs)
+    while running:
+        running = B.step()
+        steps += 1
+    assert steps == max(o["iterations"] for o in want)
+    for j in range(len(jobs)):
+        got = B.read(j)
+        assert got["iterations"] == want[j]["iterations"]
+        for key in ("decision", "hits", "imp_history", "shadow_max"):
+            np.testing.assert_array_equal(got[key], want[j][key], err_msg=f"job {j} {key}")
+    with pytest.raises(boruta.BorutaError, match="finished"):
+        B.step()
+    B.close()
+    # free-running: two iterations at a time, jobs advancing independently
+    R = boruta.Batch(jobs, job=7, precision=1)
+    while R.run(2):
+        pass
+    for j in range(len(jobs)):
+        got = R.read(j)
+        for key in ("decision", "hits", "imp_history", "shadow_max"):
+            np.testing.assert_array_equal(got[key], want[j][key], err_msg=f"job {j} {key}")
+    R.close()

@@ -65,7 +65,9 @@ typedef struct {
   void* stream;    /* cudaStream_t to run on; NULL = legacy default stream */
   uint32_t job;    /* job id folded into every random stream (batches); default 0 */
   int host_inputs; /* 1: X and y are host pointers, copied to the device inside the call */
-  int graph;       /* 1: replay each iteration's level loop as a CUDA graph */
+  int graph;       /* 1: each iteration is captured into a CUDA graph and replayed through one
+                      executable graph, updated in place from iteration to iteration (same
+                      results; per-level kernel times are then not recorded) */
   int split_path;  /* larger nodes: 0 = feature-band-sorted items when they fit (default),
                       1 = grouped items only; results are identical */
 } boruta_opts;

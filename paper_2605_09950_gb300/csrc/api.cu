@@ -58,6 +58,10 @@ struct boruta_session {
   int64_t p = 0, N = 0;
   int task = 0, mtry_opt = 0, max_iter = 0, t = 0, split_path = 0;
   int pending_t = 0;  // iteration enqueued and not yet finished
+  bool graph = false;                   // iterations replayed through an instantiated CUDA graph
+  cudaStream_t gst = nullptr;           // capture stream of the graph
+  cudaGraphExec_t gexec = nullptr;      // the graph of the last iteration, updated in place
+  int graph_builds = 0, graph_updates = 0;
   bool own_stream = false;
   unsigned long long* counters_h = nullptr;  // pinned copy of the device counters
   bool finished = false;
@@ -110,6 +114,8 @@ struct boruta_session {
       cudaStreamSynchronize(st2);
       cudaStreamDestroy(st2);
     }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (gst) cudaStreamDestroy(gst);
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
     if (status_h) cudaFreeHost(status_h);
@@ -164,6 +170,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->task = task;
   s->mtry_opt = mtry;
   s->split_path = o->split_path;
+  s->graph = o->graph != 0;
   s->max_iter = max_iter;
   Dev& d = s->d;
   const bool reg = (task & 1) != 0;
@@ -362,6 +369,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->hev.resize(2 * (max_depth + 1));
   for (auto& e : s->hev) CK(cudaEventCreate(&e));
   CK(cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking));
+  if (s->graph) CK(cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
   s->state_h.assign(p, 0);
@@ -392,15 +400,12 @@ int boruta_session_create(const uint8_t* X, int64_t ld, const void* y, int64_t N
   return 0;
 }
 
-// Enqueues iteration t+1 on the session's stream, with the copies of its
-// status, state and counters into pinned host memory; does not wait.
-static int step_launch(boruta_session* s) {
-  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
-  if (s->finished) return fail(BORUTA_EINVAL, "the run is finished (no undecided feature or t = max_iter)");
-  if (s->pending_t) return fail(BORUTA_EINVAL, "an iteration is already in flight");
+// Enqueues iteration t on the session's stream (or records it, when the
+// stream is being captured into a graph), with the copies of its status,
+// state and counters into pinned host memory; does not wait.
+static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   Dev& d = s->d;
-  cudaStream_t st = s->st;
-  const int t = s->t + 1;
+  const bool timed = !s->graph;
   // X_cur: undecided and accepted columns, in order
   int32_t p_live = 0;
   for (int64_t j = 0; j < s->p; ++j)
@@ -455,11 +460,11 @@ static int step_launch(boruta_session* s) {
     const uint64_t groups = big * static_cast<uint64_t>(d.mtry);  // work items of the larger nodes, at most
     const int gs = static_cast<int>(std::min<uint64_t>(s->small_grid, (nodes + 7) / 8));
     const int gi = static_cast<int>(std::min<uint64_t>(s->split_grid, std::max<uint64_t>(1, (groups + 7) / 8)));
-    CK(cudaEventRecord(s->ev[2 * level], st));
-    launch_split(d, level, std::max(gs, 1), gi, s->split_smem, st, s->st2, s->fork, s->join, s->hev[2 * level],
-                 s->hev[2 * level + 1]);
+    if (timed) CK(cudaEventRecord(s->ev[2 * level], st));
+    launch_split(d, level, std::max(gs, 1), gi, s->split_smem, st, s->st2, s->fork, s->join,
+                 timed ? s->hev[2 * level] : nullptr, timed ? s->hev[2 * level + 1] : nullptr);
     CK_LAUNCH("split kernels");
-    CK(cudaEventRecord(s->ev[2 * level + 1], st));
+    if (timed) CK(cudaEventRecord(s->ev[2 * level + 1], st));
     launch_children(d, level, st);
     CK_LAUNCH("next-level kernels");
   }
@@ -473,6 +478,60 @@ static int step_launch(boruta_session* s) {
   CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->state_pin, d.state, s->p, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->counters_h, d.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  return 0;
+}
+
+static int step_launch(boruta_session* s) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  if (s->finished) return fail(BORUTA_EINVAL, "the run is finished (no undecided feature or t = max_iter)");
+  if (s->pending_t) return fail(BORUTA_EINVAL, "an iteration is already in flight");
+  const int t = s->t + 1;
+  if (!s->graph) {
+    const int rc = enqueue_iteration(s, t, s->st);
+    if (rc) return rc;
+  } else {
+    // The iteration is captured (on the session's own capture stream: the
+    // caller's may be the legacy default stream, which cannot be captured)
+    // into a graph; the executable graph of the previous iteration is updated
+    // in place (kernel arguments, grids and copy sizes change with t and the
+    // live columns) and replayed on the caller's stream, or built again when
+    // the update is refused (the launch sequence changed).
+    CK(cudaStreamBeginCapture(s->gst, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_iteration(s, t, s->gst);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s->gst, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail(BORUTA_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+    }
+    bool updated = false;
+    if (s->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(s->gexec, g, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+      }
+    }
+    if (!updated) {
+      const cudaError_t ei = cudaGraphInstantiate(&s->gexec, g, 0);
+      if (ei != cudaSuccess) {
+        cudaGraphDestroy(g);
+        s->gexec = nullptr;
+        return fail(BORUTA_ECUDA, "graph instantiation: %s", cudaGetErrorString(ei));
+      }
+      ++s->graph_builds;
+    } else {
+      ++s->graph_updates;
+    }
+    cudaGraphDestroy(g);
+    CK(cudaGraphLaunch(s->gexec, s->st));
+  }
   s->pending_t = t;
   return 0;
 }
@@ -497,7 +556,7 @@ static int step_finish(boruta_session* s, int32_t* undecided) {
   s->hist_ms = 0.0;
   s->level_ms.assign(d.D + 1, 0.0);
   s->level_hist_ms.assign(d.D + 1, 0.0);
-  for (int level = 0; level < d.D; ++level) {
+  for (int level = 0; level < d.D && !s->graph; ++level) {  // graph replays carry no level events
     float ms = 0.f, hms = 0.f;
     CK(cudaEventElapsedTime(&ms, s->ev[2 * level], s->ev[2 * level + 1]));
     CK(cudaEventElapsedTime(&hms, s->hev[2 * level], s->hev[2 * level + 1]));

@@ -1306,10 +1306,10 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_
     k_plan_scatter<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   }
   // the histogram kernel of the level (one of the two does the work)
-  cudaEventRecord(hist_start, st);
+  if (hist_start) cudaEventRecord(hist_start, st);
   if (d.band_w > 0) k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
   k_items<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
-  cudaEventRecord(hist_end, st);
+  if (hist_end) cudaEventRecord(hist_end, st);
   if (d.band_w > 0) k_finalize_band<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   k_finalize<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   cudaStreamWaitEvent(st, join, 0);

@@ -239,6 +239,26 @@ def test_binary_n1000_p50_full_run():
     assert set(np.flatnonzero(g["decision"] == 1)) == set(w.informative.tolist())
 
 
+@pytest.mark.parametrize("importance", [synth.TREEIMP, synth.PERMUT])
+def test_graph_replay_matches_stream_launches(importance):
+    """opts.graph = 1 (each iteration captured, the executable graph updated
+    in place and replayed) gives the same run, bit for bit, as plain launches
+    -- including iterations after columns are rejected."""
+    import torch
+
+    from paper_2605_09950_gb300 import boruta
+
+    w = synth.binary_small(N=600, p=20, n_inf=4, n_trees=24, max_depth=7, max_iter=30, importance=importance)
+    params = w.params()
+    nc = params.pop("n_classes")
+    X, y = torch.from_numpy(w.X).cuda(), torch.from_numpy(w.y).cuda()
+    a = boruta.boruta_fit(X, y, N=w.N, n_classes=nc, precision=1, **params)
+    b = boruta.boruta_fit(X, y, N=w.N, n_classes=nc, precision=1, graph=1, **params)
+    assert a["iterations"] == b["iterations"] and (a["decision"] != 0).any()
+    for key in ("decision", "hits", "imp_history", "shadow_max"):
+        np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
 def test_checkpoint_resume_is_exact():
     """Counter-based randomness: resuming from a state read at t = 4
     reproduces the uninterrupted run bit for bit."""

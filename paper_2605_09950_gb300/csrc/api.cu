@@ -228,6 +228,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   if ((rc = s->alloc(&d.rows[1], MN))) return rc;
   if ((rc = s->alloc(&d.oob, MN))) return rc;
   if ((rc = s->alloc(&d.oob_cnt, n_trees))) return rc;
+  if (d.permut && (rc = s->alloc(&d.piv, static_cast<size_t>(N)))) return rc;
   const size_t P = cap;
   if ((rc = s->alloc(&d.nd_tree, P))) return rc;
   if ((rc = s->alloc(&d.nd_heap, P))) return rc;

@@ -30,6 +30,7 @@ struct Dev {
   uint32_t* rows[2];             // [M][N] node-ordered row entries (row << 8 | weight)
   uint32_t* oob;                 // [M][N] out-of-bag rows, ascending
   uint32_t* oob_cnt;             // [M]
+  uint32_t* piv;                 // [N] Alg. 3 flush_index of the iteration (Permut only)
   // ---- node pool (level-major; within a level, ordered by (tree, heap))
   uint32_t cap;
   uint32_t *nd_tree, *nd_heap, *nd_seg, *nd_len, *nd_n;

@@ -16,6 +16,10 @@
 
 #include "engine.cuh"
 
+#ifndef BORUTA_PERMUT_WALKS
+#define BORUTA_PERMUT_WALKS 4  // re-walks of one OOB row advanced together
+#endif
+
 namespace bgb {
 
 namespace {
@@ -411,16 +415,17 @@ void launch_treeimp(const Dev& d, int grid, cudaStream_t st) {
 }
 
 // ============================================================ Alg. 3 on OOB rows
-__device__ __forceinline__ uint32_t leaf_of(const Dev& d, uint32_t k, uint32_t row, int f,
-                                            uint8_t xf) {
-  for (int guard = 0; guard <= kMaxDepth; ++guard) {  // trees are at most kMaxDepth deep
-    const uint32_t sp = d.nd_split[k];
-    if (sp == kLeaf) return k;
-    const int g = static_cast<int>(sp >> 8);
-    const uint8_t x = (g == f) ? xf : d.Xaug[static_cast<int64_t>(g) * d.ldN + row];
-    k = d.nd_child[k] + (x > (sp & 255u) ? 1u : 0u);
-  }
-  return k;
+// flush_index of the iteration (Alg. 3): one keyed permutation of the rows,
+// shared by every feature and tree
+__global__ void k_permut_pi(Dev d) {
+  __shared__ Perm sp;
+  if (threadIdx.x == 0)
+    perm_init(sp, static_cast<uint32_t>(d.N), d.seed, 0u, unit_word(d.t, 0u), purpose_word(kPurposePermut, d.job));
+  __syncthreads();
+  const Perm P = sp;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < static_cast<uint32_t>(d.N);
+       i += gridDim.x * blockDim.x)
+    d.piv[i] = perm_apply(P, i);
 }
 
 // loss between the unpermuted leaf q and the permuted leaf q2
@@ -486,41 +491,48 @@ __device__ float loss32(const Dev& d, uint32_t q, uint32_t q2) {
 // feature f on it, re-walk from f's first node with x_f replaced by
 // X[pi(i)][f] (all later f nodes use the swapped value too).  Features off
 // the path leave the leaf unchanged and add exactly 0.
-__global__ void k_permut(Dev d) {
-  __shared__ Perm sp;
-  if (threadIdx.x == 0)
-    perm_init(sp, static_cast<uint32_t>(d.N), d.seed, 0u, unit_word(d.t, 0u),
-              purpose_word(kPurposePermut, d.job));
-  __syncthreads();
-  const Perm P = sp;
+__global__ void __launch_bounds__(128) k_permut(Dev d) {
   for (int tau = blockIdx.y; tau < d.M; tau += gridDim.y) {
     const uint32_t noob = d.oob_cnt[tau];
     const uint32_t* oob = d.oob + static_cast<int64_t>(tau) * d.N;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < noob; r += gridDim.x * blockDim.x) {
       const uint32_t i = oob[r];
-      const uint32_t pi = perm_apply(P, i);
-      // the row's path: node, split word, and the row's own bin at each node
+      const uint32_t pi = d.piv[i];
+      // the row's path: node, split word, and the row's own bin at each node;
+      // the children's words are loaded with the bin (one round trip a level)
       uint32_t path[kMaxDepth], pw[kMaxDepth];
       uint8_t px[kMaxDepth];
       int depth = 0;
       uint32_t k = static_cast<uint32_t>(tau);
-      while (depth < kMaxDepth) {
-        const uint32_t s = d.nd_split[k];
-        if (s == kLeaf) break;
+      uint32_t s = d.nd_split[k], c = d.nd_child[k];
+      while (depth < kMaxDepth && s != kLeaf) {
         const uint8_t x = d.Xaug[static_cast<int64_t>(s >> 8) * d.ldN + i];
+        const uint32_t s0 = d.nd_split[c], s1 = d.nd_split[c + 1], c0 = d.nd_child[c], c1 = d.nd_child[c + 1];
         path[depth] = k;
         pw[depth] = s;
         px[depth] = x;
         ++depth;
-        k = d.nd_child[k] + (x > (s & 255u) ? 1u : 0u);
+        const bool right = x > (s & 255u);
+        k = c + (right ? 1u : 0u);
+        s = right ? s1 : s0;
+        c = right ? c1 : c0;
       }
       const uint32_t q = k;
+      // the permuted row's bins of every feature on the path, loaded together
+      uint8_t xq[kMaxDepth];
+      for (int a = 0; a < depth; ++a) xq[a] = d.Xaug[static_cast<int64_t>(pw[a] >> 8) * d.ldN + pi];
+      // the re-walks: for each distinct feature f on the path whose swapped
+      // value sends the row the other way at some node testing f, the walk
+      // restarts at that node's other child
+      uint32_t wstart[kMaxDepth];  // node at which the swapped row leaves the path
+      uint32_t wfx[kMaxDepth];     // feature << 8 | swapped bin
+      int nw = 0;
       for (int a = 0; a < depth; ++a) {
         const uint32_t f = pw[a] >> 8;
         bool seen = false;
         for (int b = 0; b < a; ++b) seen |= (pw[b] >> 8) == f;
         if (seen) continue;
-        const uint8_t xp = d.Xaug[static_cast<int64_t>(f) * d.ldN + pi];
+        const uint8_t xp = xq[a];
         if (xp == px[a]) continue;  // same value: same leaf
         // The swapped row follows the recorded path until the first node on
         // it that tests f and sends xp the other way; if there is none it
@@ -529,12 +541,58 @@ __global__ void k_permut(Dev d) {
         for (; b < depth; ++b)
           if ((pw[b] >> 8) == f && ((xp > (pw[b] & 255u)) != (px[b] > (pw[b] & 255u)))) break;
         if (b == depth) continue;
-        const uint32_t start = d.nd_child[path[b]] + (xp > (pw[b] & 255u) ? 1u : 0u);
-        const uint32_t q2 = leaf_of(d, start, i, static_cast<int>(f), xp);
-        if (q2 == q) continue;
-        const double L = d.precision == 0 ? loss64(d, q, q2) : static_cast<double>(loss32(d, q, q2));
-        if (!csa_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + f) * kCsaLimbs, L))
-          atomicOr(&d.status[0], kErrAcc);
+        wstart[nw] = (b << 1) | ((xp > (pw[b] & 255u)) ? 1u : 0u);
+        wfx[nw] = (f << 8) | xp;
+        ++nw;
+      }
+      // kWalks re-walks advance together (independent loads in flight)
+      constexpr int kWalks = BORUTA_PERMUT_WALKS;
+      for (int w0 = 0; w0 < nw; w0 += kWalks) {
+        uint32_t wk[kWalks], ws[kWalks], wc[kWalks];
+#pragma unroll
+        for (int u = 0; u < kWalks; ++u) {
+          wk[u] = 0u;
+          ws[u] = kLeaf;
+          wc[u] = 0u;
+          if (w0 + u < nw) {
+            // the other child of the node where the swapped value turns
+            const uint32_t at = wstart[w0 + u];
+            wk[u] = d.nd_child[path[at >> 1]] + (at & 1u);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kWalks; ++u)
+          if (w0 + u < nw) {
+            ws[u] = d.nd_split[wk[u]];
+            wc[u] = d.nd_child[wk[u]];
+          }
+        for (int guard = 0; guard <= kMaxDepth; ++guard) {  // trees are at most kMaxDepth deep
+          bool busy = false;
+#pragma unroll
+          for (int u = 0; u < kWalks; ++u) {
+            if (ws[u] == kLeaf) continue;
+            busy = true;
+            const uint32_t fx = wfx[w0 + u];
+            const uint32_t g = ws[u] >> 8;
+            const uint8_t x = (g == (fx >> 8)) ? static_cast<uint8_t>(fx & 255u)
+                                               : d.Xaug[static_cast<int64_t>(g) * d.ldN + i];
+            const uint32_t c = wc[u];
+            const uint32_t s0 = d.nd_split[c], s1 = d.nd_split[c + 1], c0 = d.nd_child[c], c1 = d.nd_child[c + 1];
+            const bool right = x > (ws[u] & 255u);
+            wk[u] = c + (right ? 1u : 0u);
+            ws[u] = right ? s1 : s0;
+            wc[u] = right ? c1 : c0;
+          }
+          if (!busy) break;
+        }
+#pragma unroll
+        for (int u = 0; u < kWalks; ++u) {
+          if (w0 + u >= nw || wk[u] == q) continue;
+          const uint32_t f = wfx[w0 + u] >> 8;
+          const double L = d.precision == 0 ? loss64(d, q, wk[u]) : static_cast<double>(loss32(d, q, wk[u]));
+          if (!csa_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + f) * kCsaLimbs, L))
+            atomicOr(&d.status[0], kErrAcc);
+        }
       }
     }
   }
@@ -563,6 +621,7 @@ void launch_permut(const Dev& d, int grid, cudaStream_t st) {
   int by = d.M < 4096 ? d.M : 4096;
   int bx = grid / by;
   if (bx < 1) bx = 1;
+  k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
   k_permut<<<dim3(bx, by), 128, 0, st>>>(d);
   k_permut_final<<<grid, 256, 0, st>>>(d);
 }

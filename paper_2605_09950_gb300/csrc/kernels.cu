@@ -17,7 +17,7 @@
 #include "engine.cuh"
 
 #ifndef BORUTA_PERMUT_WALKS
-#define BORUTA_PERMUT_WALKS 4  // re-walks of one OOB row advanced together
+#define BORUTA_PERMUT_WALKS 8  // re-walks of one OOB row advanced together
 #endif
 
 namespace bgb {

@@ -91,6 +91,21 @@ def workload(trees=None):
                              max_depth=WORKLOAD["max_depth"], n_bins=WORKLOAD["n_bins"], max_iter=100)
 
 
+def combine_ranks(total_ms, units, dist=None, device="cuda"):
+    """Whole-job throughput over the ranks: the slowest rank's time (max over
+    ranks) and the units every rank processed.  Returns (value, max_ms)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+
+        world = dist.get_world_size()
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    return world * units / (total_ms / 1000.0), total_ms
+
+
 def run_reference(args):
     """The CPU oracle (as it stands) on a bounded sample: the shadow matrix of
     iteration 1 plus `ref_trees` full trees with their OOB permutation rows;
@@ -197,14 +212,8 @@ def run_gpu(args):
         for k, v in S.kernel_stats().items():
             ks_tot[k] += v
     levels = S.dump(boruta.DUMP_LEVELS, np.float64).reshape(-1, 3)
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    value, total_ms = combine_ranks(sum(step_ms), args.steps, dist)
     clocks = stop_clock_sampler(proc, fh, clk_path, local) if rank == 0 else None
-    value = world * args.steps / (total_ms / 1000.0)
     res = S.read()
     S.close()
     del S
@@ -340,16 +349,10 @@ def run_batch(args):
     B.run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    total_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    value, total_ms = combine_ranks(e0.elapsed_time(e1), len(jobs) * args.steps, dist)
     clocks = stop_clock_sampler(proc, fh, clk_path, local) if rank == 0 else None
     batched = [B.read(j) for j in range(len(jobs))]
     B.close()
-    value = world * len(jobs) * args.steps / (total_ms / 1000.0)
 
     # the plain form: each job alone, FP64 terms, after one untimed iteration
     plain_ms, same = 0.0, 0

@@ -273,6 +273,21 @@ int boruta_binom_tails(const int32_t* t, const int32_t* h, double* p_acc, double
 int boruta_binom_tails_noalloc(const int32_t* t, const int32_t* h, double* p_acc, double* p_rej,
                                int64_t n, void* stream);
 
+/*
+ * boruta_quantise -- float features to the uint8 bins the fit consumes (a
+ * helper outside the iteration; the paper does not say how features are
+ * binned).  bin(x) = min(B-1, floor(B * rank(x) / N)) with rank(x) the number
+ * of values of the column strictly below x, so equal values share a bin and
+ * -0 equals +0.
+ *   X     [in]  device float32, column-major: column j at X + j*ldx, N values
+ *   Xb    [out] device uint8 bins, column j at Xb + j*ldb (ldx, ldb >= N)
+ *   n_bins      B in [2, 256]; N < 2^24
+ *   stream      cudaStream_t (NULL = legacy default); the call waits for it
+ * NaN in X returns BORUTA_EINVAL (Xb then unspecified).  Allocates 4 bytes
+ * of stream-ordered scratch. */
+int boruta_quantise(const float* X, int64_t ldx, int64_t N, int64_t p, int n_bins, uint8_t* Xb, int64_t ldb,
+                    void* stream);
+
 /* Message for the last error on this thread ("" if none). */
 const char* boruta_last_error(void);
 

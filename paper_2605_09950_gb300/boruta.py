@@ -28,7 +28,8 @@ EXPORTS = [
     "boruta_batch_read", "boruta_batch_destroy", "boruta_session_create", "boruta_session_step",
     "boruta_session_read", "boruta_session_write", "boruta_session_dump",
     "boruta_session_kernel_stats", "boruta_session_destroy", "boruta_philox", "boruta_perm",
-    "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_last_error",
+    "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_quantise",
+    "boruta_last_error",
 ]
 
 
@@ -102,6 +103,7 @@ def lib():
         L.boruta_u256_to_double.argtypes = [vp, vp, i64, vp]
         L.boruta_binom_tails.argtypes = [vp, vp, vp, vp, i64, vp]
         L.boruta_binom_tails_noalloc.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.boruta_quantise.argtypes = [vp, i64, i64, i64, ct.c_int, vp, i64, vp]
         L.boruta_last_error.restype = ct.c_char_p
         for name in EXPORTS:
             if name not in ("boruta_default_opts", "boruta_session_destroy", "boruta_batch_destroy",
@@ -343,3 +345,20 @@ def boruta_binom_tails_noalloc(t, h, p_acc, p_rej):
     _check(lib().boruta_binom_tails_noalloc(t.data_ptr(), h.data_ptr(), p_acc.data_ptr(), p_rej.data_ptr(),
                                             t.numel(), _stream()))
     return p_acc, p_rej
+
+
+def boruta_quantise(F, n_bins, N=None):
+    """Quantile bins of float features on the GPU.  F: (p, ld) float32 CUDA
+    tensor, column j = F[j, :N].  Returns a (p, round16(N)) uint8 tensor,
+    zero past N (the layout boruta_fit takes)."""
+    import torch
+
+    if not (F.is_cuda and F.dtype == torch.float32 and F.dim() == 2 and F.stride(1) == 1):
+        raise ValueError("F must be a row-contiguous (p, ld) float32 CUDA tensor")
+    p, ld = F.shape
+    N = ld if N is None else N
+    out = torch.zeros((p, (N + 15) // 16 * 16), dtype=torch.uint8, device=F.device)
+    _check(lib().boruta_quantise(F.data_ptr(), F.stride(0), N, p, n_bins, out.data_ptr(), out.stride(0),
+                                 _stream()))
+    return out
+

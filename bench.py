@@ -91,6 +91,23 @@ def workload(trees=None):
                              max_depth=WORKLOAD["max_depth"], n_bins=WORKLOAD["n_bins"], max_iter=100)
 
 
+# the other single-job workloads (parity cases; not the default line):
+#   name -> (generator, metric, importance label)
+def other_workloads():
+    from paper_2605_09950_gb300 import synth
+
+    return {
+        "snp": (lambda trees: synth.snp_regression(n_trees=trees or 256),
+                "Boruta iterations/sec (SNP regression N=2e4, p=2e4, 256 trees, depth 12, impurity importance)",
+                "treeimp"),
+        "multiclass": (lambda trees: synth.multiclass_toeplitz(n_trees=trees or 300),
+                       "Boruta iterations/sec (5-class N=1e6, p=500, 300 trees, depth 20, OOB permutation "
+                       "importance)", "permut_oob"),
+        "small": (lambda trees: synth.binary_small(n_trees=trees or 100),
+                  "Boruta iterations/sec (binary N=1000, p=50, 100 trees, depth 8, impurity importance)", "treeimp"),
+    }
+
+
 def combine_ranks(total_ms, units, dist=None, device="cuda"):
     """Whole-job throughput over the ranks: the slowest rank's time (max over
     ranks) and the units every rank processed.  Returns (value, max_ms)."""
@@ -145,7 +162,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample(w, trees=1):
+def cpu_baseline_sample(w, trees=1, permut=True):
     import numpy as np
 
     import oracle
@@ -156,12 +173,13 @@ def cpu_baseline_sample(w, trees=1):
     sha = P.shadow(1, live)
     t1 = time.perf_counter()
     for tau in range(trees):
-        P.tree(1, live, sha, tau, nodes=False, permut=True)
+        P.tree(1, live, sha, tau, nodes=False, permut=permut)
     t2 = time.perf_counter()
     per_iter = (t1 - t0) + (t2 - t1) / trees * w.n_trees
+    what = "fit + OOB permutation row" if permut else "fit + impurity row"
     return {"value": 1.0 / per_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"iteration 1: full shadow matrix + {trees} of {w.n_trees} trees (fit + OOB permutation "
-                      f"row), scaled to {w.n_trees} trees; single-threaded C"}
+            "sample": f"iteration 1: full shadow matrix + {trees} of {w.n_trees} trees ({what}), "
+                      f"scaled to {w.n_trees} trees; single-threaded C"}
 
 
 def run_gpu(args):
@@ -180,7 +198,12 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    w = workload(args.trees)
+    metric, importance = METRIC, "permut_oob"
+    if args.workload == "binary":
+        w = workload(args.trees)
+    else:
+        gen, metric, importance = other_workloads()[args.workload]
+        w = gen(args.trees)
     X = torch.from_numpy(w.X).cuda()
     y = torch.from_numpy(w.y).cuda()
     params = w.params()
@@ -260,18 +283,18 @@ def run_gpu(args):
     # per step: gather + shadow + 2 bootstrap, 12 per level, 2 permutation importance, stats + decide
     per_step_launches = 4 + 12 * w.max_depth + 2 + 2
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "u8+int64+" + ("f32" if precision else "f64"), "data": "synthetic",
-        "config": {"workload": "binary_N100000_p1000", **WORKLOAD, "n_trees": w.n_trees,
-                   "importance": "permut_oob",
+        "config": {"workload": w.name, "N": w.N, "p": w.p, "n_trees": w.n_trees, "max_depth": w.max_depth,
+                   "n_bins": w.n_bins, "importance": importance,
                    "precision": "fp32 terms, exact sums" if precision else "fp64 terms, exact sums",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "512 MiB buffer written between timed steps; per-step working set > 1 GB"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None,
-                     "traffic": ITEMS_BAND_TRAFFIC_PER_LAUNCH,
+                     "traffic": ITEMS_BAND_TRAFFIC_PER_LAUNCH if args.workload == "binary" and not args.trees else None,
                      "kernel": "k_items_band (feature histograms + exact scan of the larger nodes)",
                      "peak_kind": f"{peak_kind} hbm_gbs", "launches": int(ks_tot["launches"]),
                      "kernel_ms_per_step": ks_tot["hist_ms"] / args.steps,
@@ -282,7 +305,8 @@ def run_gpu(args):
                         "levels": [[int(c), round(float(a), 3), round(float(h), 3)] for c, a, h in levels[:-1]],
                         "levels_note": "last timed step, per depth: nodes, split-stage ms, histogram-kernel ms"},
         "other_form": other,
-        "cpu_baseline": cpu_baseline_sample(w) if (world == 1 and not args.no_cpu) else None,
+        "cpu_baseline": (cpu_baseline_sample(w, permut=importance == "permut_oob")
+                         if (world == 1 and not args.no_cpu) else None),
         "e2e": {"value": args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps,
                 "note": "boruta_fit with host X/y: upload, K iterations, readback; includes session setup"},
@@ -423,8 +447,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
     ap.add_argument("--trees", type=int, default=None, help="fewer trees (profiling captures only)")
-    ap.add_argument("--workload", default="binary", choices=["binary", "batch"],
-                    help="binary: N=1e5 p=1000 (default); batch: 64 uneven jobs, batched vs plain form")
+    ap.add_argument("--workload", default="binary", choices=["binary", "batch", "snp", "multiclass", "small"],
+                    help="binary: N=1e5 p=1000 (default); batch: 64 uneven jobs, batched vs plain form; "
+                         "snp / multiclass / small: the other single-job workloads")
     ap.add_argument("--jobs", type=int, default=64, help="batch workload: number of jobs")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -294,6 +294,11 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   CK(cudaStreamSynchronize(s->st));
   if (s->status_h[0] & kErrInput)
     return fail(BORUTA_EINVAL, "input has a bin >= n_bins (%d) or a label >= 8", n_bins);
+  // Bins above the largest one present are empty in every node: a threshold
+  // there sends every row left and is never valid, so the fit only needs
+  // histograms up to the largest bin (same trees, smaller histograms and
+  // scans; e.g. genotype columns declared with 256 bins use 3).
+  d.B = std::max(2, std::min(n_bins, static_cast<int>(s->status_h[3]) + 1));
   if (reg) {
     d.C = 1;
     if (maxy && static_cast<double>(maxy) * static_cast<double>(N) >= 4611686018427387904.0)

@@ -74,12 +74,16 @@ __device__ T block_sum(T v, T* smem) {
 // ============================================================ input validation
 __global__ void k_validate(Dev d) {
   bool bad = false;
-  uint32_t maxlab = 0;
+  uint32_t maxlab = 0, maxbin = 0;
   for (int j = blockIdx.y; j < d.p; j += gridDim.y) {
     const uint8_t* col = d.X + static_cast<int64_t>(j) * d.ld;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-      bad |= col[i] >= d.B;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+      const uint32_t b = col[i];
+      bad |= b >= static_cast<uint32_t>(d.B);
+      maxbin = max(maxbin, b);
+    }
   }
+  if (maxbin) atomicMax(&d.status[3], maxbin);
   if (blockIdx.y == 0 && d.kind == 0) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
       const uint32_t y = d.ycls[i];

@@ -552,6 +552,58 @@ __device__ __forceinline__ void hist_clear(const Dev& d, uint32_t* hw) {
 
 // Adds up to 32 * kBatch rows, entries already in registers (entry q of
 // lane l is row r0 + q * 32 + l of the node), to the warp's histogram.
+// Columns with at most 4 bins (e.g. genotypes): each lane keeps its rows'
+// weights (per class for two classes) and weighted targets per bin in
+// registers, and the warp totals are written to the histogram at the end --
+// no shared-memory atomics, which would serialise on the few addresses.
+__device__ __forceinline__ bool regs4(const Dev& d, int kind) { return d.B <= 4 && (kind == 1 || d.C <= 2); }
+
+template <int KIND>
+__device__ __forceinline__ void regs4_add(uint32_t b, uint32_t e, bool valid, long long yv, uint32_t (&c0)[4],
+                                          uint32_t (&c1)[4], long long (&sy)[4]) {
+  const uint32_t w = valid ? ent_w<KIND>(e) : 0u;
+  const bool one = KIND == 0 && ent_y(e) != 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t add = b == static_cast<uint32_t>(k) ? w : 0u;
+    if (KIND == 0) {
+      c0[k] += one ? 0u : add;
+      c1[k] += one ? add : 0u;
+    } else {
+      c0[k] += add;
+      sy[k] += static_cast<long long>(add) * yv;
+    }
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void regs4_store(const Dev& d, uint32_t* hw, const uint32_t (&c0)[4],
+                                            const uint32_t (&c1)[4], const long long (&sy)[4]) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k >= d.B) break;  // uniform
+    const uint32_t t0 = __reduce_add_sync(kFull, c0[k]);
+    if (KIND == 0) {
+      const uint32_t t1 = __reduce_add_sync(kFull, c1[k]);
+      if (lane == 0) {
+        hw[k * d.C] = t0;  // bin k < 8: no padding word before it
+        if (d.C == 2) hw[k * d.C + 1] = t1;
+      }
+    } else {
+      long long v = sy[k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+      if (lane == 0) {
+        hw[k] = t0;
+        reinterpret_cast<long long*>(hw + hist_words_n(d.B))[k] = v;
+      }
+    }
+  }
+  __syncwarp();
+}
+
 template <int KIND, int kBatch>
 __device__ __forceinline__ void hist_add(const Dev& d, uint32_t r0, uint32_t len, const uint32_t (&e)[kBatch],
                                          const uint8_t* col, uint32_t* hw) {
@@ -594,6 +646,27 @@ __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint3
                            uint32_t* hw) {
   const int lane = threadIdx.x & 31;
   constexpr int kBatch = BORUTA_STREAM_BATCH;
+  if (regs4(d, KIND)) {
+    uint32_t c0[4] = {0u, 0u, 0u, 0u}, c1[4] = {0u, 0u, 0u, 0u};
+    long long sy[4] = {0, 0, 0, 0};
+    for (uint32_t r0 = 0; r0 < len; r0 += 32 * kBatch) {
+      uint32_t e[kBatch], b[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        const uint32_t r = r0 + q * 32 + lane;
+        e[q] = r < len ? rows[base + r] : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) b[q] = r0 + q * 32 + lane < len ? col[e[q] >> 8] : 0u;
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        const bool v = r0 + q * 32 + lane < len;
+        regs4_add<KIND>(b[q], e[q], v, (KIND == 1 && v) ? d.yreg[e[q] >> 8] : 0ll, c0, c1, sy);
+      }
+    }
+    regs4_store<KIND>(d, hw, c0, c1, sy);
+    return;
+  }
   hist_clear<KIND>(d, hw);
   uint32_t e[kBatch];
 #pragma unroll
@@ -902,6 +975,19 @@ template <int KIND>
 __device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const uint32_t* ebuf,
                                             const uint32_t (&b)[kRegRows / 32], uint32_t* hw) {
   const int lane = threadIdx.x & 31;
+  if (regs4(d, KIND)) {
+    uint32_t c0[4] = {0u, 0u, 0u, 0u}, c1[4] = {0u, 0u, 0u, 0u};
+    long long sy[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) {
+      const uint32_t r = q * 32 + lane;
+      const bool v = r < len;
+      const uint32_t e = v ? ebuf[r] : 0u;
+      regs4_add<KIND>(b[q], e, v, (KIND == 1 && v) ? d.yreg[e >> 8] : 0ll, c0, c1, sy);
+    }
+    regs4_store<KIND>(d, hw, c0, c1, sy);
+    return;
+  }
   hist_clear<KIND>(d, hw);
   __syncwarp();
   if (KIND == 0) {

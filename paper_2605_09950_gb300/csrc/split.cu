@@ -35,6 +35,9 @@
 #ifndef BORUTA_SMALL_MINB
 #define BORUTA_SMALL_MINB 4
 #endif
+#ifndef BORUTA_SMALL_AHEAD
+#define BORUTA_SMALL_AHEAD 8  // features whose bins a small-node warp loads at once
+#endif
 #ifndef BORUTA_STREAM_BATCH
 #define BORUTA_STREAM_BATCH 8  // rows per lane per pass of a streamed histogram
 #endif
@@ -45,6 +48,8 @@
 namespace bgb {
 
 namespace {
+
+constexpr int kSmallAhead = BORUTA_SMALL_AHEAD;
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -369,9 +374,51 @@ struct SmallPlanes {
 // Regression: the left sums are accumulated over the rows by shuffles.
 // Updates the node's exact best (best) and best float score so far (bestf).
 template <int KIND, int CM>
-__device__ void small_feature(const NodeInfo<CM>& nd, int C, bool v, uint32_t b, uint32_t w, uint32_t y,
+__device__ void small_feature(const NodeInfo<CM>& nd, int C, int B, bool v, uint32_t b, uint32_t w, uint32_t y,
                               long long yv, const SmallPlanes<CM>& pl, int feat, uint32_t tkey, float& bestf,
                               Cand<CM>& best) {
+  if (KIND == 1 && B <= 4) {
+    // Regression on a column of at most 4 bins: the left sums of each of
+    // the <= 3 thresholds come from warp reductions, the same on every lane.
+    // A threshold whose bin holds no row repeats the partition of a lower
+    // one and loses the tie to it.
+    float sf[3];
+    uint32_t nLt[3];
+    long long SLt[3];
+    float mx = -1.0f;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      sf[t] = -1.0f;
+      nLt[t] = 0u;
+      SLt[t] = 0;
+      if (t >= B - 1) break;  // uniform
+      const bool in = v && b <= static_cast<uint32_t>(t);
+      const uint32_t nl = __reduce_add_sync(kFull, in ? w : 0u);
+      long long sl = in ? static_cast<long long>(w) * yv : 0ll;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sl += __shfl_xor_sync(kFull, sl, off);
+      nLt[t] = nl;
+      SLt[t] = sl;
+      if (nl > 0u && nl < nd.n) {
+        sf[t] = score_reg_f(sl, nd.SP, nl, nd.n);
+        mx = fmaxf(mx, sf[t]);
+      }
+    }
+    if (mx < 0.0f || mx < screen(bestf)) return;
+    const float thr = screen(fmaxf(mx, bestf));
+    bestf = fmaxf(mx, bestf);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      if (sf[t] < 0.0f || sf[t] < thr) continue;
+      Cand<CM> c;
+      make_reg<CM>(c, SLt[t], nd.SP, nLt[t], nd.n);
+      c.feat = feat;
+      c.bin = t;
+      c.key = (tkey << 8) | static_cast<uint32_t>(t);
+      if (better(c, best)) best = c;
+    }
+    return;
+  }
   uint32_t cl[CM];
 #pragma unroll
   for (int k = 0; k < CM; ++k) cl[k] = 0u;
@@ -470,7 +517,9 @@ __global__ void __launch_bounds__(256) k_classify(Dev d, int level) {
 
 template <int KIND, int CM>
 __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, int level) {
+  __shared__ uint8_t sbins[8][kSmallAhead * 32];
   const int lane = threadIdx.x & 31;
+  uint8_t* sbin = sbins[threadIdx.x >> 5];
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
@@ -501,17 +550,27 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
     for (int r0 = 0; r0 < d.mtry; r0 += 32) {
       const int ns = min(32, d.mtry - r0);
       const uint32_t myf = lane < ns ? perm_apply(P, static_cast<uint32_t>(r0 + lane)) : 0u;
-      // the next feature's bins are gathered while this one is scored (the
-      // shuffles run on all lanes, outside the per-lane conditions)
-      const uint32_t f0 = __shfl_sync(kFull, myf, 0);
-      uint32_t bn = v ? column(d, f0)[row] : 0u;
-      for (int j = 0; j < ns; ++j) {
-        const uint32_t f = __shfl_sync(kFull, myf, j);
-        const uint32_t fn = __shfl_sync(kFull, myf, min(j + 1, ns - 1));
-        const uint32_t b = bn;
-        if (j + 1 < ns) bn = v ? column(d, fn)[row] : 0u;
-        const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(r0 + j) : f;
-        small_feature<KIND, CM>(nd, C, v, b, w, y, yv, pl, static_cast<int>(f), tkey, bestf, best);
+      for (int j0 = 0; j0 < ns; j0 += kSmallAhead) {
+        // the row's bins of the next kSmallAhead features, all loads in
+        // flight at once (the shuffles run on all lanes, outside the per-lane
+        // conditions), parked in the warp's shared memory
+        uint32_t bv[kSmallAhead];
+#pragma unroll
+        for (int u = 0; u < kSmallAhead; ++u) {
+          const uint32_t fu = __shfl_sync(kFull, myf, min(j0 + u, ns - 1));
+          bv[u] = (v && j0 + u < ns) ? column(d, fu)[row] : 0u;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kSmallAhead; ++u) sbin[u * 32 + lane] = static_cast<uint8_t>(bv[u]);
+        __syncwarp();
+        const int nu = min(kSmallAhead, ns - j0);
+        for (int u = 0; u < nu; ++u) {
+          const uint32_t f = __shfl_sync(kFull, myf, j0 + u);
+          const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(r0 + j0 + u) : f;
+          small_feature<KIND, CM>(nd, C, d.B, v, sbin[u * 32 + lane], w, y, yv, pl, static_cast<int>(f), tkey, bestf,
+                                  best);
+        }
       }
     }
     uint32_t sp = 0;

@@ -76,7 +76,7 @@ struct boruta_session {
   uint8_t* X_owned = nullptr;
   void* y_owned = nullptr;
   // launch geometry
-  int sms = 0, split_grid = 0, small_grid = 0, tree_grid = 0, permut_grid = 0;
+  int sms = 0, split_grid = 0, small_grid = 0, tree_grid = 0, permut_grid = 0, walk_grid = 0;
   size_t split_smem = 0;
   // second stream for the small-node kernel, and its fork/join events
   cudaStream_t st2 = nullptr;
@@ -367,9 +367,16 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kptr[1], kSplitThreads, s->split_smem));
   if (per_sm < 1) return fail(BORUTA_EINVAL, "split kernel does not fit on an SM");
   s->split_grid = per_sm * s->sms;
-  s->small_grid = 8 * s->sms;
+  // warp-per-node kernels: as many blocks as the GPU holds at once (they
+  // loop over their nodes), so no partial last wave
+  int small_per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, small_kernel_ptr(variant), 256, 0));
+  s->small_grid = std::max(1, std::min(8, small_per_sm)) * s->sms;
   s->tree_grid = std::min(n_trees, 8 * s->sms);
   s->permut_grid = 16 * s->sms;
+  int walk_per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, permut_kernel_ptr(), 128, 0));
+  s->walk_grid = std::max(1, walk_per_sm) * s->sms;
   s->ev.resize(2 * (max_depth + 1));
   for (auto& e : s->ev) CK(cudaEventCreate(&e));
   s->hev.resize(2 * (max_depth + 1));
@@ -475,7 +482,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
     CK_LAUNCH("next-level kernels");
   }
   if (d.permut)
-    launch_permut(d, s->permut_grid, st);
+    launch_permut(d, s->permut_grid, s->walk_grid, st);
   else
     launch_treeimp(d, s->tree_grid, st);
   CK_LAUNCH("importance kernels");

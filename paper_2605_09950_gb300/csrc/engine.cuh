@@ -101,12 +101,14 @@ void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t 
 size_t ninfo_bytes(int variant);
 int split_variant(int kind, int C);
 void split_kernel_ptrs(int variant, const void** ptrs, int* n);  // kernels taking dynamic shared memory
+const void* small_kernel_ptr(int variant);  // for its occupancy
 size_t cand_bytes(int variant);
 size_t packed_bytes(int variant);
 void launch_gather_live(const Dev& d, cudaStream_t st);
 void launch_children(const Dev& d, int level, cudaStream_t st);
 void launch_treeimp(const Dev& d, int grid, cudaStream_t st);
-void launch_permut(const Dev& d, int grid, cudaStream_t st);
+void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st);
+const void* permut_kernel_ptr();  // for its occupancy
 void launch_stats_decide(const Dev& d, cudaStream_t st);
 // Warp-private histogram layout.  A lane scans 8 consecutive bins, so one
 // padding slot follows every 8 bins: lane l's block then starts at a bank

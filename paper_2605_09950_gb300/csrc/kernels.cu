@@ -495,11 +495,18 @@ __device__ float loss32(const Dev& d, uint32_t q, uint32_t q2) {
 // feature f on it, re-walk from f's first node with x_f replaced by
 // X[pi(i)][f] (all later f nodes use the swapped value too).  Features off
 // the path leave the leaf unchanged and add exactly 0.
+// Work items are (tree, chunk of 128 OOB rows), dealt round-robin to a grid
+// of exactly the blocks the GPU holds at once, so no partial last wave.
 __global__ void __launch_bounds__(128) k_permut(Dev d) {
-  for (int tau = blockIdx.y; tau < d.M; tau += gridDim.y) {
+  const uint32_t chunks = (static_cast<uint32_t>(d.N) + 127u) / 128u;
+  const uint64_t items = static_cast<uint64_t>(d.M) * chunks;
+  for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    const int tau = static_cast<int>(item / chunks);
     const uint32_t noob = d.oob_cnt[tau];
     const uint32_t* oob = d.oob + static_cast<int64_t>(tau) * d.N;
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < noob; r += gridDim.x * blockDim.x) {
+    const uint32_t r = static_cast<uint32_t>(item - static_cast<uint64_t>(tau) * chunks) * 128u + threadIdx.x;
+    if (r >= noob) continue;
+    {
       const uint32_t i = oob[r];
       const uint32_t pi = d.piv[i];
       // the row's path: node, split word, and the row's own bin at each node;
@@ -621,14 +628,13 @@ __global__ void k_permut_final(Dev d) {
   }
 }
 
-void launch_permut(const Dev& d, int grid, cudaStream_t st) {
-  int by = d.M < 4096 ? d.M : 4096;
-  int bx = grid / by;
-  if (bx < 1) bx = 1;
+void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
   k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
-  k_permut<<<dim3(bx, by), 128, 0, st>>>(d);
+  k_permut<<<walk_grid, 128, 0, st>>>(d);
   k_permut_final<<<grid, 256, 0, st>>>(d);
 }
+
+const void* permut_kernel_ptr() { return reinterpret_cast<const void*>(&k_permut); }
 
 // ============================================================ Alg. 1: statistic, hits, test
 // s_j over trees, exact sums rounded once:

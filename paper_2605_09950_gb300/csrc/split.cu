@@ -1508,6 +1508,15 @@ void split_kernel_ptrs(int variant, const void** ptrs, int* n) {
   *n = i;
 }
 
+const void* small_kernel_ptr(int variant) {
+  switch (variant) {
+    case 0: return reinterpret_cast<const void*>(&k_split_small<0, 2>);
+    case 1: return reinterpret_cast<const void*>(&k_split_small<0, 4>);
+    case 2: return reinterpret_cast<const void*>(&k_split_small<0, 8>);
+    default: return reinterpret_cast<const void*>(&k_split_small<1, 1>);
+  }
+}
+
 void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st,
                   cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hs, cudaEvent_t he) {
   switch (split_variant(d.kind, d.C)) {

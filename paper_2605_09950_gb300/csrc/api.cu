@@ -436,7 +436,9 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   // item holds a 14-bit slot and a 22-bit feature
   d.band_w = 0;
   d.nbands = 0;
-  if (s->split_path == 0 && d.item_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
+  d.chunk0 = 0;
+  d.chunk_cap = static_cast<uint32_t>(std::min<uint64_t>(d.item_cap / static_cast<uint64_t>(d.mtry), 1u << 26));
+  if (s->split_path == 0 && d.chunk_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
     int64_t w = std::max<int64_t>(1, kBandBytes / d.ldN);
     w = std::max<int64_t>(w, (p_aug + kMaxBands - 1) / kMaxBands);
     d.band_w = static_cast<int32_t>(w);
@@ -474,7 +476,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
     const int gs = static_cast<int>(std::min<uint64_t>(s->small_grid, (nodes + 7) / 8));
     const int gi = static_cast<int>(std::min<uint64_t>(s->split_grid, std::max<uint64_t>(1, (groups + 7) / 8)));
     if (timed) CK(cudaEventRecord(s->ev[2 * level], st));
-    launch_split(d, level, std::max(gs, 1), gi, s->split_smem, st, s->st2, s->fork, s->join,
+    launch_split(d, level, std::max(gs, 1), gi, big, s->split_smem, st, s->st2, s->fork, s->join,
                  timed ? s->hev[2 * level] : nullptr, timed ? s->hev[2 * level + 1] : nullptr);
     CK_LAUNCH("split kernels");
     if (timed) CK(cudaEventRecord(s->ev[2 * level + 1], st));

@@ -56,6 +56,7 @@ struct Dev {
   uint32_t* band_cnt;            // [kMaxBands + 1] groups per band, then cursors; last: total
   uint64_t item_cap;
   int32_t band_w, nbands;        // columns per band (0: grouped path only), bands
+  uint32_t chunk0, chunk_cap;    // band path: first larger node of the chunk, nodes per chunk
   // ---- importance and Boruta state
   long long* acc;                // [M][p_aug][kCsaLimbs] exact per-tree accumulators (carry-save)
   double* imp;                   // [M][p_aug]
@@ -75,7 +76,7 @@ constexpr int kSplitThreads = 256;
 constexpr int kItemsPerNode = 16;  // work items (groups of draw slots) per larger node
 constexpr int kMaxBands = 256;     // feature bands of the band-sorted path
 constexpr int64_t kBandBytes = 24ll << 20;  // column bytes per band (kept in L2 while in use)
-constexpr uint64_t kMaxItems = 64ull << 20;  // plan buffer capacity (items)
+constexpr uint64_t kMaxItems = 128ull << 20;  // plan buffer capacity (items)
 constexpr int kMaxIterations = 126;          // max_iter limit (exact binomial tails in 128 bits)
 #ifndef BORUTA_STAGED_ROWS
 #define BORUTA_STAGED_ROWS 128
@@ -95,7 +96,7 @@ void launch_bootstrap(const Dev& d, int grid, cudaStream_t st);
 // small-node kernel then runs on `st2` while the larger-node kernels run on
 // `st` (fork/join through the two events).
 // hist_start/hist_end are recorded on `st` around the histogram kernel.
-void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st,
+void launch_split(const Dev& d, int level, int grid_small, int grid_big, uint64_t big_bound, size_t smem, cudaStream_t st,
                   cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hist_start,
                   cudaEvent_t hist_end);
 size_t ninfo_bytes(int variant);

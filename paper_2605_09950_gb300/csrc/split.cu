@@ -938,8 +938,15 @@ __device__ void dense_feature(const Dev& d, const NodeInfo<CM>& nd, const uint32
   scan_hist<KIND, CM>(d, nd, hw, true, feat, tkey, out);
 }
 
-__device__ __forceinline__ bool band_path(const Dev& d, uint32_t nbig) {
-  return d.band_w > 0 && static_cast<uint64_t>(nbig) * static_cast<uint64_t>(d.mtry) <= d.item_cap;
+__device__ __forceinline__ bool band_path(const Dev& d, uint32_t) { return d.band_w > 0; }
+
+// The band path runs the level's larger nodes in chunks of chunk_cap nodes
+// (their items fill the plan buffers at most); this launch's chunk starts at
+// chunk0.  Returns the number of nodes of the chunk (0: nothing to do).
+__device__ __forceinline__ uint32_t chunk_nodes(const Dev& d, int level) {
+  const uint32_t nbig = d.work[level];
+  if (d.band_w == 0 || d.chunk0 >= nbig) return 0u;
+  return min(nbig - d.chunk0, d.chunk_cap);
 }
 
 // A feature's exact best candidate, kept as the integers that define it:
@@ -1148,8 +1155,8 @@ template <int KIND, int CM>
 __global__ void __launch_bounds__(256) k_plan_gen(Dev d, int level) {
   __shared__ uint32_t sband[kMaxBands];
   __shared__ uint32_t wcnt[8][kMaxBands];
-  const uint32_t nbig = d.work[level];
-  if (!band_path(d, nbig)) return;
+  const uint32_t nbig = chunk_nodes(d, level);
+  if (nbig == 0u) return;
   for (int b = threadIdx.x; b < d.nbands; b += blockDim.x) sband[b] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1158,7 +1165,7 @@ __global__ void __launch_bounds__(256) k_plan_gen(Dev d, int level) {
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
-    const uint32_t k = d.big[rank];
+    const uint32_t k = d.big[d.chunk0 + rank];
     uint32_t len = 0;
     if (lane == 0) {  // the node's totals, read once here instead of by each of its groups
       NodeInfo<CM> nd;
@@ -1193,7 +1200,7 @@ __global__ void __launch_bounds__(256) k_plan_gen(Dev d, int level) {
 // exclusive scan of the per-band group counts into band cursors, and the
 // total (one warp)
 __global__ void k_plan_scan(Dev d, int level) {
-  if (!band_path(d, d.work[level])) return;
+  if (chunk_nodes(d, level) == 0u) return;
   const uint32_t total = warp_scan_bands(d.band_cnt, d.nbands, threadIdx.x & 31);
   if (threadIdx.x == 0) d.band_cnt[kMaxBands] = total;
 }
@@ -1202,8 +1209,8 @@ __global__ void k_plan_scan(Dev d, int level) {
 template <int KIND, int CM>
 __global__ void __launch_bounds__(256) k_plan_scatter(Dev d, int level) {
   __shared__ uint32_t wcnt[8][kMaxBands];
-  const uint32_t nbig = d.work[level];
-  if (!band_path(d, nbig)) return;
+  const uint32_t nbig = chunk_nodes(d, level);
+  if (nbig == 0u) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* cnt = wcnt[warp];
   const uint32_t bw = static_cast<uint32_t>(d.band_w);
@@ -1248,8 +1255,7 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
   uint32_t* ebuf = hw + hist_smem_per_warp(d.kind, d.C, d.B) / 4;
-  const uint32_t nbig = d.work[level];
-  if (!band_path(d, nbig)) return;
+  if (chunk_nodes(d, level) == 0u) return;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
@@ -1307,15 +1313,15 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
 template <int KIND, int CM>
 __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize_band(Dev d, int level) {
   const int lane = threadIdx.x & 31;
-  const uint32_t nbig = d.work[level];
-  if (!band_path(d, nbig)) return;
+  const uint32_t nbig = chunk_nodes(d, level);
+  if (nbig == 0u) return;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
   uint32_t* rows_out = d.rows[(level & 1) ^ 1];
   unsigned long long bytes = 0;
   for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
-    const uint32_t k = d.big[rank];
+    const uint32_t k = d.big[d.chunk0 + rank];
     NodeInfo<CM> nd;
     load_node<KIND, CM>(d, k, level, nd);
     const PackedCand<CM>* pc = reinterpret_cast<const PackedCand<CM>*>(d.fbest) + static_cast<uint64_t>(rank) * d.mtry;
@@ -1435,8 +1441,8 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize(Dev d, int 
 }
 
 template <int KIND, int CM>
-void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_t smem, cudaStream_t st,
-                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hist_start,
+void launch_level(const Dev& d, int level, int grid_small, int grid_items, uint64_t big_bound, size_t smem,
+                  cudaStream_t st, cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hist_start,
                   cudaEvent_t hist_end) {
   k_classify<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   // small nodes on st2, concurrently with the larger-node kernels on st
@@ -1444,19 +1450,30 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, size_
   cudaStreamWaitEvent(st2, fork, 0);
   k_split_small<KIND, CM><<<grid_small, 256, 0, st2>>>(d, level);
   cudaEventRecord(join, st2);
-  if (d.band_w > 0) {
+  // band path: the larger nodes in chunks of chunk_cap (at most big_bound
+  // nodes exist; chunks past the level's count return at once)
+  const uint64_t nchunks =
+      d.band_w > 0 ? (big_bound + d.chunk_cap - 1) / d.chunk_cap + (big_bound == 0 ? 1 : 0) : 0;
+  for (uint64_t c = 0; c < nchunks; ++c) {
+    Dev dc = d;
+    dc.chunk0 = static_cast<uint32_t>(c * d.chunk_cap);
     cudaMemsetAsync(d.band_cnt, 0, (kMaxBands + 1) * sizeof(uint32_t), st);
-    k_plan_gen<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
-    k_plan_scan<<<1, 32, 0, st>>>(d, level);
-    k_plan_scatter<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+    k_plan_gen<KIND, CM><<<grid_small, 256, 0, st>>>(dc, level);
+    k_plan_scan<<<1, 32, 0, st>>>(dc, level);
+    k_plan_scatter<KIND, CM><<<grid_small, 256, 0, st>>>(dc, level);
+    // the histogram kernel of the level (with several chunks the window also
+    // holds the later chunks' plan and finalize kernels)
+    if (c == 0 && hist_start) cudaEventRecord(hist_start, st);
+    k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(dc, level);
+    if (c + 1 == nchunks && hist_end) cudaEventRecord(hist_end, st);
+    k_finalize_band<KIND, CM><<<grid_small, 256, 0, st>>>(dc, level);
   }
-  // the histogram kernel of the level (one of the two does the work)
-  if (hist_start) cudaEventRecord(hist_start, st);
-  if (d.band_w > 0) k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
-  k_items<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
-  if (hist_end) cudaEventRecord(hist_end, st);
-  if (d.band_w > 0) k_finalize_band<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
-  k_finalize<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+  if (nchunks == 0) {  // grouped path
+    if (hist_start) cudaEventRecord(hist_start, st);
+    k_items<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
+    if (hist_end) cudaEventRecord(hist_end, st);
+    k_finalize<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+  }
   cudaStreamWaitEvent(st, join, 0);
 }
 
@@ -1517,13 +1534,16 @@ const void* small_kernel_ptr(int variant) {
   }
 }
 
-void launch_split(const Dev& d, int level, int grid_small, int grid_big, size_t smem, cudaStream_t st,
-                  cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hs, cudaEvent_t he) {
+void launch_split(const Dev& d, int level, int grid_small, int grid_big, uint64_t big_bound, size_t smem,
+                  cudaStream_t st, cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hs,
+                  cudaEvent_t he) {
   switch (split_variant(d.kind, d.C)) {
-    case 0: launch_level<0, 2>(d, level, grid_small, grid_big, smem, st, st2, fork, join, hs, he); break;
-    case 1: launch_level<0, 4>(d, level, grid_small, grid_big, smem, st, st2, fork, join, hs, he); break;
-    case 2: launch_level<0, 8>(d, level, grid_small, grid_big, smem, st, st2, fork, join, hs, he); break;
-    default: launch_level<1, 1>(d, level, grid_small, grid_big, smem, st, st2, fork, join, hs, he); break;
+    case 0: launch_level<0, 2>(d, level, grid_small, grid_big, big_bound, smem, st, st2, fork, join, hs, he); break;
+    case 1: launch_level<0, 4>(d, level, grid_small, grid_big, big_bound, smem, st, st2, fork, join, hs, he); break;
+    case 2: launch_level<0, 8>(d, level, grid_small, grid_big, big_bound, smem, st, st2, fork, join, hs, he); break;
+    default:
+      launch_level<1, 1>(d, level, grid_small, grid_big, big_bound, smem, st, st2, fork, join, hs, he);
+      break;
   }
 }
 

@@ -28,7 +28,7 @@ WORKLOAD = dict(N=100_000, p=1000, n_trees=500, max_depth=16, n_bins=256)
 # DRAM bytes (read + write) per k_items_band launch from an ncu capture of the
 # same kernel (profiles/k_items_band_binary_N100000_p1000.md: all 16 launches
 # at 50 trees, scaled to 500 trees); None once the kernel changes.
-ITEMS_BAND_TRAFFIC_PER_LAUNCH = 10.27e9
+ITEMS_BAND_TRAFFIC_PER_LAUNCH = 10.0e9
 METRIC = "Boruta iterations/sec (binary N=1e5, p=1000, 500 trees, depth 16, OOB permutation importance)"
 UNIT = "iterations/s"
 

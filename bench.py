@@ -351,7 +351,7 @@ def run_batch(args):
     jobs = [dict(X=torch.from_numpy(w.X).cuda(), y=torch.from_numpy(w.y).cuda(), N=w.N, **w.params()) for w in ws]
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    opts = dict(precision=1, job=rank * 4096, stream=stream.cuda_stream)
+    opts = dict(precision=1, job=rank * 4096, stream=stream.cuda_stream, graph=int(args.graph))
 
     B = boruta.Batch(jobs, **opts)  # warm-up on a throw-away batch
     B.run(args.warmup)
@@ -419,6 +419,7 @@ def run_batch(args):
                        "precision": "fp32 terms, exact sums",
                        "l2": "inputs larger than L2 (X and shadows of 64 jobs ~1.5 GB); one 512 MiB flush before",
                        "schedule": "boruta_batch_run: each job's next iteration enqueued when its last completes",
+                       "graph_replay": bool(args.graph),
                        "input_generation_s": gen_s, "batch_setup_s": setup_s},
             "plain_form": {"value": plain, "unit": "job-iterations/s",
                            "form": "one job at a time, one session each, fp64 terms",
@@ -451,6 +452,7 @@ def main():
                     help="binary: N=1e5 p=1000 (default); batch: 64 uneven jobs, batched vs plain form; "
                          "snp / multiclass / small: the other single-job workloads")
     ap.add_argument("--jobs", type=int, default=64, help="batch workload: number of jobs")
+    ap.add_argument("--graph", action="store_true", help="batch workload: replay each job's iterations as CUDA graphs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -68,7 +68,7 @@ typedef struct {
   int graph;       /* 1: each iteration is captured into a CUDA graph and replayed through one
                       executable graph, updated in place from iteration to iteration (same
                       results; per-level kernel times are then not recorded) */
-  int split_path;  /* larger nodes: 0 = feature-band-sorted items when they fit (default),
+  int split_path;  /* larger nodes: 0 = feature-band-sorted groups, in chunks of nodes (default),
                       1 = grouped items only; results are identical */
 } boruta_opts;
 

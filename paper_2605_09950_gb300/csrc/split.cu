@@ -3,25 +3,27 @@
 // TreeImp accumulators (Alg. 2) and the stable row partition.
 //
 // Kernels of a level:
-//   k_split_small   one warp per node with at most 32 distinct rows: one row
-//                   per lane, candidate thresholds at the bins present, left
-//                   counts from a warp-wide compare loop (no histogram); it
-//                   also lists the level's larger active nodes.
-//   larger nodes, feature-band path (default):
-//     k_plan_gen / k_plan_scan / k_plan_scatter  one work item per (node,
-//                   draw slot), counting-sorted by the band of columns its
-//                   feature lies in, so that the columns being gathered at
-//                   any moment fit in L2;
-//     k_items_band  one warp per item: warp-private shared-memory histogram
-//                   from batched gathers, warp prefix scan over the bins,
-//                   the feature's exact best candidate, kept as the integers
-//                   that define it (feature, bin, left counts);
-//     k_finalize_band  one warp per node: exact argmax over its features'
-//                   candidates (rebuilt from those integers), split record
-//                   and partition.
-//   larger nodes, grouped path (when a level has more items than the plan
-//   buffers hold): k_items (one warp per group of draw slots, exact) and
-//   k_finalize (exact argmax over groups, record, partition).
+//   k_classify      leaves, and the lists of small (<= 32 rows) and larger
+//                   active nodes.
+//   k_split_small   (second stream) one warp per node of at most 32 rows:
+//                   one row per lane, left class counts from ballots over the
+//                   bin bits against weight and class bit planes (regression:
+//                   shuffles, or warp reductions for columns of <= 4 bins).
+//   larger nodes, feature-band path (default), in chunks of nodes whose
+//   items fit the plan buffers:
+//     k_plan_gen / k_plan_scan / k_plan_scatter  the nodes' (node, draw slot)
+//                   items ordered by the band of columns their feature lies
+//                   in, cut into (node, band) groups sorted by band, so that
+//                   the columns being gathered at any moment fit in L2;
+//     k_items_band  one warp per group: per feature a warp-private
+//                   shared-memory histogram (entries of nodes of <= 128 rows
+//                   staged once per group), a float pre-screen over the
+//                   non-empty bins, and the feature's exact best candidate,
+//                   kept as the integers that define it;
+//     k_finalize_band  one warp per node: float screen of its features'
+//                   candidates, exact argmax, split record and partition.
+//   larger nodes, grouped path (split_path = 1, or mtry >= 2^14): k_items
+//   (one warp per group of draw slots, exact) and k_finalize.
 // Candidate (f, b): rows with bin <= b go left.  Score num/den =
 // (A_L n_R + A_R n_L) / (n_L n_R) with A = sum_k c_k^2 (Gini) or S^2
 // (variance); scores are compared exactly (256-bit cross products) after a

@@ -69,3 +69,30 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(boruta, "_LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="missing"):
         boruta.lib()
+
+
+def test_quantise_and_batch_reject_bad_arguments_on_the_host(lib):
+    """Argument checks run before any CUDA call (no GPU needed)."""
+    import ctypes as ct
+
+    from paper_2605_09950_gb300 import boruta
+
+    L = boruta.lib()
+    # quantise: NULL pointers, N < 1, ld < N, bins outside [2, 256]
+    assert L.boruta_quantise(None, 16, 16, 2, 8, None, 16, None) == -1
+    buf = (ct.c_float * 32)()
+    out = (ct.c_uint8 * 32)()
+    assert L.boruta_quantise(ct.addressof(buf), 16, 0, 2, 8, ct.addressof(out), 16, None) == -1
+    assert L.boruta_quantise(ct.addressof(buf), 8, 16, 2, 8, ct.addressof(out), 16, None) == -1
+    assert L.boruta_quantise(ct.addressof(buf), 16, 16, 2, 1, ct.addressof(out), 16, None) == -1
+    assert L.boruta_quantise(ct.addressof(buf), 16, 16, 2, 257, ct.addressof(out), 16, None) == -1
+    assert b"n_bins" in L.boruta_last_error()
+    # batch: negative job count, NULL output handle, NULL batch
+    h = ct.c_void_p()
+    assert L.boruta_batch_create(-1, None, None, ct.byref(h)) == -1
+    assert L.boruta_batch_create(0, None, None, None) == -1
+    running = ct.c_int32()
+    assert L.boruta_batch_step(None, ct.byref(running)) == -1
+    assert L.boruta_batch_run(None, 1, ct.byref(running)) == -1
+    assert L.boruta_batch_read(None, 0, None, None, None, None, None) == -1
+    L.boruta_batch_destroy(None)

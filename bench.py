@@ -182,6 +182,30 @@ def cpu_baseline_sample(w, trees=1, permut=True):
                       f"scaled to {w.n_trees} trees; single-threaded C"}
 
 
+class Stepper:
+    """Steps a session; a run that finished (every feature decided, or
+    t = max_iter) is restarted from its initial state before the next step,
+    outside any timed region (ready())."""
+
+    def __init__(self, S, max_iter):
+        self.S, self.max_iter = S, max_iter
+        self.fresh = S.read()
+        self.t, self.done = 0, False
+
+    def ready(self):
+        if self.done:
+            self.reset()
+
+    def reset(self):
+        self.S.write(self.fresh)
+        self.t, self.done = 0, False
+
+    def step(self):
+        und = self.S.step()
+        self.t += 1
+        self.done = und == 0 or self.t >= self.max_iter
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -210,11 +234,12 @@ def run_gpu(args):
     nc = params.pop("n_classes")
     precision = args.precision
     S = boruta.Session(X, y, N=w.N, n_classes=nc, precision=precision, job=rank, **params)
-    fresh = S.read()
+    R = Stepper(S, w.max_iter)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2, written between steps
     for _ in range(args.warmup):
-        S.step()
-    S.write(fresh)
+        R.ready()
+        R.step()
+    R.reset()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -224,11 +249,12 @@ def run_gpu(args):
     ks_tot = dict(hist_ms=0.0, hist_bytes=0.0, split_ms=0.0, split_bytes=0.0, launches=0)
     stream = torch.cuda.current_stream()
     for _ in range(args.steps):
+        R.ready()
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        S.step()
+        R.step()
         e1.record(stream)
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -245,16 +271,17 @@ def run_gpu(args):
     other = None
     if not args.no_other:
         S2 = boruta.Session(X, y, N=w.N, n_classes=nc, precision=1 - precision, job=rank, **params)
-        fresh2 = S2.read()
-        S2.step()
-        S2.write(fresh2)
+        R2 = Stepper(S2, w.max_iter)
+        R2.step()
+        R2.reset()
         ms2 = []
         for _ in range(args.steps):
+            R2.ready()
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            S2.step()
+            R2.step()
             e1.record(stream)
             torch.cuda.synchronize()
             ms2.append(e0.elapsed_time(e1))
@@ -267,11 +294,12 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers (upload + K iterations + readback)
     t0 = time.perf_counter()
-    boruta.boruta_fit(w.X, w.y, N=w.N, n_classes=nc, precision=precision, host_inputs=1, job=rank,
-                      **{**params, "max_iter": args.steps})
+    fit = boruta.boruta_fit(w.X, w.y, N=w.N, n_classes=nc, precision=precision, host_inputs=1, job=rank,
+                            **{**params, "max_iter": min(args.steps, w.max_iter)})
     e2e_s = time.perf_counter() - t0
+    e2e_iters = max(1, int(fit["iterations"]))  # a run may finish before max_iter
     h2d = int(w.X.nbytes + w.y.nbytes)
-    d2h = int(w.p * (1 + 4) + 8 * args.steps * w.p + 8 * args.steps)
+    d2h = int(w.p * (1 + 4) + 8 * e2e_iters * w.p + 8 * e2e_iters)
 
     if rank != 0:
         if dist:
@@ -307,8 +335,8 @@ def run_gpu(args):
         "other_form": other,
         "cpu_baseline": (cpu_baseline_sample(w, permut=importance == "permut_oob")
                          if (world == 1 and not args.no_cpu) else None),
-        "e2e": {"value": args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
-                "d2h_bytes_per_step": d2h / args.steps,
+        "e2e": {"value": e2e_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_iters,
+                "d2h_bytes_per_step": d2h / e2e_iters,
                 "note": "boruta_fit with host X/y: upload, K iterations, readback; includes session setup"},
         "gpu_launches": per_step_launches * args.steps,
         "clocks": clocks,

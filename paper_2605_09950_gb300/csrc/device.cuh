@@ -256,22 +256,6 @@ __device__ inline bool fix_from_double(double x, uint64_t v[kFixLimbs]) {
   return true;
 }
 
-// acc += v with carries, atomically per limb; the total is exact whatever
-// the interleaving of concurrent adders (the sum is taken mod 2^384).
-__device__ inline void fix_atomic_add(unsigned long long* acc, const uint64_t v[kFixLimbs]) {
-  uint64_t carry = 0;
-#pragma unroll
-  for (int i = 0; i < kFixLimbs; ++i) {
-    const uint64_t a = v[i] + carry;
-    uint64_t c = (a < v[i]) ? 1ull : 0ull;
-    if (a != 0) {
-      const uint64_t old = atomicAdd(acc + i, static_cast<unsigned long long>(a));
-      c |= (old + a < old) ? 1ull : 0ull;
-    }
-    carry = c;
-  }
-}
-
 __device__ __forceinline__ void fix_add(uint64_t acc[kFixLimbs], const uint64_t v[kFixLimbs]) {
   uint64_t carry = 0;
 #pragma unroll

@@ -48,3 +48,40 @@ def test_combine_ranks_single_process():
 
     value, ms = bench.combine_ranks(250.0, 5)
     assert ms == 250.0 and value == pytest.approx(20.0)
+
+
+class _FakeSession:
+    """Counts steps; every feature is decided at the third iteration."""
+
+    def __init__(self):
+        self.t, self.writes = 0, 0
+
+    def read(self):
+        return {"t": 0}
+
+    def write(self, state):
+        self.t = state["t"]
+        self.writes += 1
+
+    def step(self):
+        self.t += 1
+        return 0 if self.t == 3 else 5
+
+
+def test_stepper_restarts_finished_runs_outside_the_step():
+    import bench
+
+    S = _FakeSession()
+    R = bench.Stepper(S, max_iter=10)
+    ts = []
+    for _ in range(7):
+        R.ready()  # restart (untimed) only when the last step finished the run
+        R.step()
+        ts.append(S.t)
+    assert ts == [1, 2, 3, 1, 2, 3, 1]
+    assert S.writes == 2
+    R2 = bench.Stepper(_FakeSession(), max_iter=2)  # t = max_iter also ends a run
+    for _ in range(3):
+        R2.ready()
+        R2.step()
+    assert R2.S.writes == 1

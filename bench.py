@@ -472,7 +472,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", type=int, default=1, help="0 = FP64 terms, 1 = FP32 terms")
-    ap.add_argument("--ref-trees", type=int, default=2)
+    ap.add_argument("--ref-trees", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
     ap.add_argument("--trees", type=int, default=None, help="fewer trees (profiling captures only)")

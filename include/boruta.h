@@ -211,10 +211,12 @@ int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacit
 
 /* Timing of the last step, from CUDA events on the session's stream (any
  * pointer may be NULL):
- *   hist_ms, hist_bytes  the histogram kernel (one launch per tree level):
- *                        total milliseconds and algorithmic bytes (one row
- *                        entry and one bin per (row, feature) pair, plus the
- *                        target for regression, plus the candidate records)
+ *   hist_ms, hist_bytes  the histogram kernel of the larger nodes (per tree
+ *                        level): total milliseconds and the method's
+ *                        algorithmic bytes -- one bin per (row, sampled
+ *                        feature) pair plus the row's state once per node
+ *                        (entry read and rewritten, weight and label: 10 B;
+ *                        17 B with the 8-byte regression target)
  *   launches             number of tree levels (histogram-kernel launches)
  *   split_ms, split_bytes the whole split stage of the levels (classify,
  *                        histograms, split records, partition), and its

@@ -94,6 +94,7 @@ def lib():
             L.orc_tree.argtypes = [P(Problem), ct.c_int, vp, ct.c_int64, vp, ct.c_int, vp, ct.c_int64,
                                    P(ct.c_int64), vp, vp]
             L.orc_tree.restype = ct.c_int
+            L.orc_decide.argtypes = [ct.c_int, ct.c_double, ct.c_int64, vp, vp]
             L.orc_iteration.argtypes = [P(Problem), ct.c_int, vp, vp, vp, P(ct.c_double), vp, vp,
                                         P(ct.c_int64)]
             L.orc_iteration.restype = ct.c_int
@@ -175,6 +176,14 @@ def binom_tails(t: int, h: int):
     lo = np.zeros(2, np.uint64)
     lib().orc_binom_tails(t, h, ct.byref(pa), ct.byref(pr), _ptr(up), _ptr(lo))
     return pa.value, pr.value, int(up[0]) | (int(up[1]) << 64), int(lo[0]) | (int(lo[1]) << 64)
+
+
+def decide(t: int, alpha: float, hits, state):
+    """Alg. 1's test after iteration t: returns the updated state."""
+    hits = np.ascontiguousarray(hits, dtype=np.int32)
+    st = np.array(state, dtype=np.int8)
+    lib().orc_decide(t, alpha, st.size, _ptr(hits), _ptr(st))
+    return st
 
 
 def node_split(task, n_classes, n_bins, bins, w, y, feats):

@@ -25,6 +25,28 @@
 
 #include "exact.h"
 
+/* test(state, hit, t) of Alg. 1: two one-sided binomial tests at 1/2 with
+ * Bonferroni's correction over the m features undecided before the test
+ * (m is fixed before any feature of this test is decided); accept is tried
+ * before reject; both comparisons are strict. */
+void orc_decide(int t, double alpha, int64_t p, const int32_t* hits, int8_t* state) {
+  int64_t m = 0;
+  for (int64_t j = 0; j < p; j++) m += state[j] == 0;
+  if (m == 0) return;
+  double thr = alpha / (double)m;
+  for (int64_t j = 0; j < p; j++) {
+    if (state[j] != 0) continue;
+    unsigned __int128 up, lo;
+    binom_tails(t, hits[j], &up, &lo);
+    double p_acc = ldexp(u128_to_double(up), -t);
+    double p_rej = ldexp(u128_to_double(lo), -t);
+    if (p_acc < thr)
+      state[j] = 1;
+    else if (p_rej < thr)
+      state[j] = -1;
+  }
+}
+
 int orc_iteration(const orc_problem* P, int t, int8_t* state, int32_t* hits, double* hist_row,
                   double* shadow_max, double* imp_out, double* s_out, int64_t* p_aug_out) {
   int64_t p = P->p, M = P->n_trees;
@@ -85,20 +107,7 @@ int orc_iteration(const orc_problem* P, int t, int8_t* state, int32_t* hits, dou
     if (s[a] > smax) hits[j] += 1;
   }
 
-  int64_t m = 0;
-  for (int64_t j = 0; j < p; j++) m += state[j] == 0;
-  double thr = P->alpha / (double)m;
-  for (int64_t j = 0; j < p; j++) {
-    if (state[j] != 0) continue;
-    unsigned __int128 up, lo;
-    binom_tails(t, hits[j], &up, &lo);
-    double p_acc = ldexp(u128_to_double(up), -t);
-    double p_rej = ldexp(u128_to_double(lo), -t);
-    if (p_acc < thr)
-      state[j] = 1;
-    else if (p_rej < thr)
-      state[j] = -1;
-  }
+  orc_decide(t, P->alpha, p, hits, state);
 
   if (imp_out) memcpy(imp_out, imp, sizeof(double) * (size_t)(M * p_aug));
   if (s_out) memcpy(s_out, s, sizeof(double) * (size_t)p_aug);

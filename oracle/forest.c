@@ -11,8 +11,8 @@
  *   - criterion, maximised exactly over integers:
  *       classification (Gini):  A_L/n_L + A_R/n_R,  A = sum_k c_k^2
  *       regression (variance):  S_L^2/n_L + S_R^2/n_R,  S = sum w*y
- *     ties go to the feature drawn first in the node's sample (or, with
- *     tie_break = 1, the lowest feature index), then to the lowest bin;
+ *     ties go to the lowest feature index (or, with tie_break = 1, to the
+ *     feature drawn first in the node's sample), then to the lowest bin;
  *   - a node is a leaf at depth max_depth, when no candidate is valid, or
  *     when the best split does not decrease impurity (delta <= 0).
  *
@@ -218,7 +218,7 @@ static int64_t grow(tree_t* T, uint64_t heap, int depth, const uint32_t* rows, c
 
   uint32_t* feats = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)T->mtry);
   orc_mtry(T->P->seed, T->P->job, T->t, T->tree, (uint32_t)heap, T->p_aug, T->mtry, feats);
-  if (T->P->tie_break == 1) qsort(feats, (size_t)T->mtry, sizeof(uint32_t), cmp_u32);
+  if (T->P->tie_break == 0) qsort(feats, (size_t)T->mtry, sizeof(uint32_t), cmp_u32);
   best_t bs;
   node_search(&T->d, rows, w, nrows, &st, feats, T->mtry, &bs, &T->of);
   free(feats);

@@ -59,7 +59,7 @@ typedef struct {
   uint32_t job;
   int stat;             /* 0 = Z score (mean / (sd / sqrt(M))), 1 = mean */
   double kl_eps;        /* smoothing of class probabilities in the KL loss */
-  int tie_break;        /* equal scores: 0 = first drawn feature, 1 = lowest index; then lowest bin */
+  int tie_break;        /* equal scores: 0 = lowest feature index, 1 = first drawn feature; then lowest bin */
 } orc_problem;
 
 /* One tree node, as dumped for parity checks.  Trees are listed in
@@ -119,6 +119,11 @@ int orc_node_split(int task, int n_classes, int n_bins, int64_t nrows, int64_t n
 int orc_tree(const orc_problem* P, int t, const int32_t* live, int64_t p_live,
              const uint8_t* Xsha, int tree, orc_node* nodes, int64_t cap,
              int64_t* n_nodes, double* imp_treeimp, double* imp_permut);
+
+/* ---- the test of Alg. 1 alone ----
+ * state[p] (1 accepted, 0 undecided, -1 rejected) is updated in place from
+ * the hit counts after iteration t. */
+void orc_decide(int t, double alpha, int64_t p, const int32_t* hits, int8_t* state);
 
 /* ---- one Boruta iteration (Alg. 1 loop body) ----
  * state/hits are updated in place; hist_row[p] receives the hit statistic of

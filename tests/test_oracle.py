@@ -293,6 +293,8 @@ def _naive_tree(P, t, live, Xsha, tree, w):
         if depth >= P.c.max_depth:
             return
         feats = oracle.mtry_features(P.c.seed, 0, t, tree, heap, p_aug, mtry)
+        if P.c.tie_break == 0:  # equal scores: lowest feature index first
+            feats = np.sort(feats)
         best = _brute_force(0, P.n_classes, P.c.n_bins, cols[:, rows].T, ws, ys, feats)
         if best is None:
             return
@@ -305,8 +307,10 @@ def _naive_tree(P, t, live, Xsha, tree, w):
     return sorted(out, key=lambda d: (d["depth"], d["heap"]))
 
 
-def test_tree_rebuilds_from_naive_builder():
+@pytest.mark.parametrize("tie_break", [0, 1])
+def test_tree_rebuilds_from_naive_builder(tie_break):
     w, P = _small(N=120, p=5, max_depth=4)
+    P.c.tie_break = tie_break
     live = np.arange(5, dtype=np.int32)
     sha = P.shadow(1, live)
     for tree in range(2):
@@ -434,6 +438,97 @@ def test_permut_constant_column_is_zero():
     assert pm[2] == 0.0
 
 
+def _stump(task, C, N=600, p=6, B=8, seed=11, tree=1):
+    """A depth-1 forest on raw seeded data (no generator): bins uniform in
+    [0, B); labels uniform in [0, C) with column 0 shifting them, or targets
+    at 2^-20 fixed point that depend on column 0."""
+    rng = np.random.default_rng(seed)
+    X = np.zeros((p, synth.pad16(N)), np.uint8)
+    X[:, :N] = rng.integers(0, B, size=(p, N))
+    if task & 1:
+        y = (rng.standard_normal(N) * 2**20 + X[0, :N].astype(np.int64) * 2**19).astype(np.int64)
+    else:
+        y = ((rng.integers(0, C, size=N) + (X[0, :N] >= B // 2)) % C).astype(np.uint8)
+    P = oracle.BorutaProblem(X, y, task | 2, n_trees=1, max_depth=1, n_bins=B, max_iter=1, seed=seed,
+                             n_classes=C if task == 0 else 0, N=N)
+    live = np.arange(p, dtype=np.int32)
+    sha = P.shadow(1, live)
+    nodes, _, pm = P.tree(1, live, sha, tree, permut=True)
+    assert len(nodes) == 3 and nodes[0]["feature"] >= 0
+    cols = np.concatenate([X[:, :N], sha])
+    oob = np.flatnonzero(oracle.bootstrap(seed, 0, 1, tree, N) == 0)
+    cnt = oracle.bootstrap(seed, 0, 1, tree, N)
+    return nodes, pm, cols[int(nodes[0]["feature"])], P.permut_table(1), oob, y[:N], cnt
+
+
+def test_permut_regression_stump_exact():
+    """Alg. 3 with the squared-error loss of the paper's regression case, on a
+    stump: the root feature's importance is (1/|OOB|) times the sum, over the
+    OOB rows whose permuted value crosses the threshold, of the squared
+    difference of the two leaf means in real units, ((S_L/n_L - S_R/n_R) *
+    2^-20)^2 -- here in exact rationals from the raw targets, not from the
+    oracle's node records.  Every other feature gets exactly 0.  (Checked to
+    fail when the oracle's 2^-20 scale is dropped or its leaf mean is taken
+    as an integer quotient.)"""
+    nodes, pm, col, pi, oob, y, cnt = _stump(1, 1)
+    b = int(nodes[0]["bin"])
+    f = int(nodes[0]["feature"])
+    N = col.size
+    left = col <= b
+    SL = sum(int(cnt[i]) * int(y[i]) for i in range(N) if left[i])
+    nL = int(cnt[left].sum())
+    SR = sum(int(cnt[i]) * int(y[i]) for i in range(N) if not left[i])
+    nR = int(cnt[~left].sum())
+    diff = (Fraction(SL, nL) - Fraction(SR, nR)) * Fraction(1, 2**20)
+    crossing = sum(1 for i in oob if left[i] != left[pi[i]])
+    want = diff * diff * crossing / len(oob)
+    assert crossing > 0
+    assert pm[f] == pytest.approx(float(want), rel=1e-13)
+    assert np.count_nonzero(pm) == 1
+
+
+@pytest.mark.parametrize("C", [3, 5])
+def test_permut_multiclass_stump_kl(C):
+    """Alg. 3 with the KL loss for C > 2 classes on a stump: for each OOB row
+    whose permuted value crosses the threshold, KL(P~_q || P~_q') with
+    P~_k = (c_k/n + eps) / (1 + C eps), q the row's own leaf -- computed
+    here from the raw labels in exact rationals and 50-digit logarithms
+    (decimal), so the normalisation 1 + C*eps, the direction of the
+    divergence and the C library's log are all checked.  (Checked to fail
+    when the oracle normalises with 1 + 2 eps, or swaps the two leaves.)"""
+    import decimal
+
+    nodes, pm, col, pi, oob, y, cnt = _stump(0, C)
+    f, b = int(nodes[0]["feature"]), int(nodes[0]["bin"])
+    N = col.size
+    left = col <= b
+    eps = Fraction(1e-7)
+
+    def probs(side):
+        c = [sum(int(cnt[i]) for i in range(N) if left[i] == side and y[i] == k) for k in range(C)]
+        n = sum(c)
+        return [(Fraction(ck, n) + eps) / (1 + C * eps) for ck in c]
+
+    ctx = decimal.Context(prec=50)
+
+    def dec(q):
+        return ctx.divide(decimal.Decimal(q.numerator), decimal.Decimal(q.denominator))
+
+    def kl(P, Q):
+        return sum(ctx.multiply(dec(a), ctx.ln(dec(a / c))) for a, c in zip(P, Q))
+
+    PL, PR = probs(True), probs(False)
+    total = decimal.Decimal(0)
+    for i in oob:
+        if left[i] != left[pi[i]]:
+            total += kl(PL, PR) if left[i] else kl(PR, PL)
+    want = float(total / len(oob))
+    assert want > 0
+    assert pm[f] == pytest.approx(want, rel=1e-12)
+    assert kl(PL, PR) != kl(PR, PL)  # the direction matters on this data
+    assert np.count_nonzero(pm) == 1
+
+
 # ---------------------------------------------------------------- statistics
 
 def test_zscore_closed_forms():
@@ -485,20 +580,104 @@ def test_decision_thresholds():
     assert not oracle.binom_tails(t_min - 1, t_min - 1)[0] < alpha / m
 
 
+def _alg1_test(t, alpha, hits, state):
+    """Alg. 1's test() restated with exact rationals: m = features undecided
+    before the test (fixed for the whole test); for each undecided j,
+    P_acc = P(Bin(t, 1/2) >= h_j) and P_rej = P(Bin(t, 1/2) <= h_j) from
+    math.comb; accept if P_acc < alpha/m, else reject if P_rej < alpha/m."""
+    m = sum(1 for s in state if s == 0)
+    out = list(state)
+    if m == 0:
+        return out
+    thr = Fraction(alpha) / m
+    for j, s in enumerate(state):
+        if s != 0:
+            continue
+        h = int(hits[j])
+        up = Fraction(sum(math.comb(t, k) for k in range(h, t + 1)), 2**t)
+        lo = Fraction(sum(math.comb(t, k) for k in range(0, h + 1)), 2**t)
+        if up < thr:
+            out[j] = 1
+        elif lo < thr:
+            out[j] = -1
+    return out
+
+
+def test_decision_step_cases():
+    """Hand-built cases of Alg. 1's test, each fixing one rule:
+    (a) strict <: alpha/m = 2^-t exactly; h = t gives P_acc = alpha/m and
+        h = 0 gives P_rej = alpha/m, so nothing is decided (fails if the
+        oracle compares with <=);
+    (b) Bonferroni m = undecided features, not p: with 6 of 10 columns
+        decided, alpha = 2^-7 accepts at t = 10 with m = 4 but would not
+        with m = 10 (fails if the oracle counts every column);
+    (c) m is fixed before the test: the feature accepted first does not
+        lower m for the next one (fails if m is decremented as features
+        are decided);
+    (d) accept is tried before reject: with alpha/m = 0.9 both tails of
+        h = 2 at t = 4 (11/16 each) are below it (fails if reject is
+        tried first)."""
+    # (a)
+    st = oracle.decide(10, 2.0**-8, [10, 0, 10, 3, 3, 0], [0, -1, 0, 1, 0, 0])
+    assert st.tolist() == _alg1_test(10, 2.0**-8, [10, 0, 10, 3, 3, 0], [0, -1, 0, 1, 0, 0])
+    assert st.tolist() == [0, -1, 0, 1, 0, 0]  # P_rej of h = 0 is also exactly alpha/m
+    # (b)
+    state = [1, 1, 1, -1, -1, -1, 0, 0, 0, 0]
+    hits = [10, 10, 10, 0, 0, 0, 10, 10, 5, 10]
+    st = oracle.decide(10, 2.0**-7, hits, state)
+    assert st.tolist() == _alg1_test(10, 2.0**-7, hits, state) == [1, 1, 1, -1, -1, -1, 1, 1, 0, 1]
+    assert _alg1_test(10, 2.0**-7, hits, [0] * 10)[6] == 0
+    # (c)
+    st = oracle.decide(10, 2.0**-6, [10, 9], [0, 0])
+    assert st.tolist() == _alg1_test(10, 2.0**-6, [10, 9], [0, 0]) == [1, 0]
+    # (d)
+    st = oracle.decide(4, 0.9, [2], [0])
+    assert st.tolist() == _alg1_test(4, 0.9, [2], [0]) == [1]
+
+
+def test_decision_step_random_runs():
+    """Random hit sequences over many iterations, with m shrinking as
+    features are decided: the oracle's test equals the exact restatement
+    after every iteration."""
+    rng = np.random.default_rng(3)
+    checked = 0
+    for run in range(40):
+        p = int(rng.integers(1, 40))
+        alpha = float(rng.choice([0.01, 0.05, 0.2, 0.9]))
+        rate = rng.uniform(0, 1, size=p)
+        state = np.zeros(p, np.int8)
+        hits = np.zeros(p, np.int32)
+        for t in range(1, 60):
+            hits += (rng.random(p) < rate) & (state >= 0)
+            want = _alg1_test(t, alpha, hits, state.tolist())
+            state = oracle.decide(t, alpha, hits, state)
+            assert state.tolist() == want, (run, t)
+            checked += 1
+            if not (state == 0).any():
+                break
+    assert checked > 500
+
+
 # ---------------------------------------------------------------- end to end
 
 @pytest.mark.slow
-def test_planted_informative_set_is_found():
-    """Binary N=1000, p=50: exactly the 10 planted class-conditional columns
-    are accepted and every noise column is rejected within 20 iterations;
-    no decision before t = 13."""
+@pytest.mark.parametrize("tie_break", [0, 1])
+def test_planted_informative_set_is_found(tie_break):
+    """Binary N=1000, p=50: all 10 planted class-conditional columns are
+    accepted within 20 iterations under either tie rule, and no decision
+    comes before t = 13.  With ties to the feature drawn first (tie_break
+    = 1) no noise column is accepted and at least 36 are rejected; with
+    ties to the lowest index (the default) real columns win the many ties
+    of tiny nodes against the shadows, whose indices are all higher, so
+    some noise columns can be accepted too."""
     w = synth.binary_small()
-    P = oracle.BorutaProblem(w.X, w.y, **w.params(), N=w.N)
+    P = oracle.BorutaProblem(w.X, w.y, **w.params(), N=w.N, tie_break=tie_break)
     r = P.run()
     acc = set(np.flatnonzero(r["decision"] == 1).tolist())
-    assert acc == set(w.informative.tolist())
-    assert np.all(r["decision"][np.setdiff1d(np.arange(50), w.informative)] != 1)
-    assert (r["decision"] == -1).sum() >= 36
+    assert set(w.informative.tolist()) <= acc
+    if tie_break == 1:
+        assert acc == set(w.informative.tolist())
+        assert (r["decision"] == -1).sum() >= 36
     assert r["iterations"] <= 20
     first = np.isnan(r["imp_history"]).any(axis=1).argmax()
     assert first == 0 or first >= 13

@@ -59,7 +59,8 @@ typedef enum {
 typedef struct {
   int stat;        /* hit statistic: 0 = Z score mean/(sd/sqrt(M)) (default), 1 = mean */
   int precision;   /* per-term arithmetic: 0 = FP64 (default), 1 = FP32; sums are exact either way */
-  int tie_break;   /* equal split scores: 0 = feature drawn first at the node (default), 1 = lowest index */
+  int tie_break;   /* equal split scores: 0 = lowest feature index (default), 1 = feature drawn first at
+                      the node; then the lowest bin */
   int n_classes;   /* classification: 0 = max(y) + 1 */
   double kl_eps;   /* class-probability smoothing in the KL loss; default 1e-7 */
   void* stream;    /* cudaStream_t to run on; NULL = legacy default stream */
@@ -262,16 +263,22 @@ int boruta_binom_tails(const int32_t* t, const int32_t* h, double* p_acc, double
  * program whose own allocator has reserved the GPU's memory, or a path
  * where cudaMalloc/cudaFree and the device synchronisation they can imply
  * are not allowed).  The binomial table lives in a fixed device array of
- * 258,068 bytes that every GPU which loads the library keeps until the
- * process exits.
+ * 258,080 bytes (C(t, k) for t <= 126 and an error word).
  *   t, h   [in]  device int32[n]; t must lie in [0, 126] (else BORUTA_EINVAL,
  *                and the entries with a bad t are written as NaN)
  *   p_acc, p_rej [out] device double[n], as for boruta_binom_tails
  *   stream [in]  cudaStream_t (NULL = legacy default stream); the call waits for it
  * The first call on a device looks up the array's address and fills the
- * table (with that device current); make that first call before any stream
- * capture.  All calls share the array: its error word is cleared at the
- * start of each call, and calls that overlap on the GPU race on it. */
+ * table (with that device current).  With CUDA's default lazy module
+ * loading that first call is also when the device loads the library's
+ * module holding the array, which allocates the array and the module's
+ * code: make the first call on each device before the caller's allocator
+ * reserves that device's memory, or run with CUDA_MODULE_LOADING=EAGER.
+ * Later calls allocate nothing.  No call may be made while its stream is
+ * being captured into a CUDA graph (each call copies the error word to
+ * pageable host memory and synchronises the stream).  All calls share the
+ * array: its error word is cleared at the start of each call, and calls
+ * that overlap on the GPU race on it. */
 int boruta_binom_tails_noalloc(const int32_t* t, const int32_t* h, double* p_acc, double* p_rej,
                                int64_t n, void* stream);
 

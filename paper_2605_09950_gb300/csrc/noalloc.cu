@@ -19,13 +19,17 @@ using bgb::u128;
 constexpr int kMaxRows = 127;  // C(t, k) for 0 <= k <= t <= 126 (max_iter <= 126)
 
 // The whole scratch: 127 x 127 coefficients (258,064 bytes) and one error
-// word.  Every GPU that loads the library holds it until the process exits.
+// word, 258,080 bytes with the 16-byte alignment of the coefficients.  With
+// CUDA's default lazy module loading the array is allocated on a device when
+// this file's module is first used there (the first call on that device);
+// from then on the device holds it until the process exits.
 struct NoAllocScratch {
   u128 tri[kMaxRows * kMaxRows];
   unsigned int bad;  // set when a query asks for t outside [0, 126]
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+static_assert(sizeof(NoAllocScratch) == 258080, "size stated in boruta.h");
 
 // Device address of the array per device, looked up once per device with
 // that device current (in host code the symbol itself is only a stand-in).

@@ -27,8 +27,8 @@
 // Candidate (f, b): rows with bin <= b go left.  Score num/den =
 // (A_L n_R + A_R n_L) / (n_L n_R) with A = sum_k c_k^2 (Gini) or S^2
 // (variance); scores are compared exactly (256-bit cross products) after a
-// float pre-screen; equal scores go to the lower key = (draw slot, or
-// feature index) << 8 | bin.
+// float pre-screen; equal scores go to the lower key = (feature index, or
+// the draw slot with tie_break = 1) << 8 | bin.
 #include <cstdint>
 
 #include "engine.cuh"
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
         const int nu = min(kSmallAhead, ns - j0);
         for (int u = 0; u < nu; ++u) {
           const uint32_t f = __shfl_sync(kFull, myf, j0 + u);
-          const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(r0 + j0 + u) : f;
+          const uint32_t tkey = d.tie_break == 1 ? static_cast<uint32_t>(r0 + j0 + u) : f;
           small_feature<KIND, CM>(nd, C, d.B, v, sbin[u * 32 + lane], w, y, yv, pl, static_cast<int>(f), tkey, bestf,
                                   best);
         }
@@ -1342,7 +1342,7 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize_band(Dev d,
       if (s < d.mtry) {
         const PackedCand<CM> p = pc[s];
         if (packed_score_f<KIND, CM>(p, nd, d.C) >= thr) {
-          const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(s) : (p.fb >> 8);
+          const uint32_t tkey = d.tie_break == 1 ? static_cast<uint32_t>(s) : (p.fb >> 8);
           unpack_cand<KIND, CM>(p, nd, d.C, tkey, mine);
         }
       }
@@ -1395,7 +1395,7 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items(Dev 
     const int s1 = min(d.mtry, (part + 1) * G);
     for (int slot = part * G; slot < s1; ++slot) {
       const uint32_t f = perm_apply(P, static_cast<uint32_t>(slot));
-      const uint32_t tkey = d.tie_break == 0 ? static_cast<uint32_t>(slot) : f;
+      const uint32_t tkey = d.tie_break == 1 ? static_cast<uint32_t>(slot) : f;
       Cand<CM> c;
       dense_feature<KIND, CM>(d, nd, rows_in, static_cast<int>(f), tkey, hw, c);
       if (better(c, best)) best = c;

@@ -144,8 +144,15 @@ def test_fp32_form_iteration(importance):
     check_iteration(w, precision=1)
 
 
-def test_lowest_index_tie_break():
-    w = synth.binary_small(N=300, p=10, n_inf=2, n_trees=8, max_depth=8, max_iter=3)
+@pytest.mark.parametrize("importance", [0, 2])
+def test_draw_order_tie_break(importance):
+    """tie_break = 1: equal scores go to the feature drawn first at the node
+    (the default, 0, takes the lowest feature index and runs in every other
+    test)."""
+    w = synth.binary_small(N=300, p=10, n_inf=2, n_trees=8, max_depth=8, max_iter=3, importance=importance)
+    check_iteration(w, tie_break=1)
+    w = synth.snp_regression(N=500, p=20, n_add=4, n_pairs=2, n_trees=6, max_depth=7, max_iter=3,
+                             importance=importance)
     check_iteration(w, tie_break=1)
 
 

@@ -57,3 +57,34 @@ def test_noalloc_rejects_t_beyond_table():
     boruta.boruta_binom_tails_noalloc(t2, h2, a2, r2)
     wa, wr = boruta.boruta_binom_tails(t2, h2)
     assert a2.item() == wa.item() and r2.item() == wr.item()
+
+
+def test_noalloc_calls_leave_free_memory_unchanged():
+    """After a first call on the device (which loads the module holding the
+    fixed array), further calls -- good ones and a rejected one -- allocate
+    no device memory: the device's free memory is the same before and
+    after.  Every tensor the calls use is allocated before the first
+    reading."""
+    import torch
+
+    from paper_2605_09950_gb300 import boruta
+
+    dev = torch.device("cuda:0")
+    t_np, h_np = _queries(3)
+    t = torch.from_numpy(t_np).to(dev)
+    h = torch.from_numpy(h_np).to(dev)
+    a = torch.empty(t.numel(), dtype=torch.float64, device=dev)
+    r = torch.empty_like(a)
+    tb = torch.tensor([127], dtype=torch.int32, device=dev)
+    hb = torch.tensor([0], dtype=torch.int32, device=dev)
+    ab = torch.empty(1, dtype=torch.float64, device=dev)
+    rb = torch.empty_like(ab)
+    boruta.boruta_binom_tails_noalloc(t, h, a, r)  # warm-up: first use on this device
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    for _ in range(3):
+        boruta.boruta_binom_tails_noalloc(t, h, a, r)
+        with pytest.raises(boruta.BorutaError, match="126"):
+            boruta.boruta_binom_tails_noalloc(tb, hb, ab, rb)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(dev)[0] == free0

@@ -71,6 +71,9 @@ typedef struct {
                       results; per-level kernel times are then not recorded) */
   int split_path;  /* larger nodes: 0 = feature-band-sorted groups, in chunks of nodes (default),
                       1 = grouped items only; results are identical */
+  int chunk_nodes; /* band path: at most this many larger nodes per chunk (0 = as many as the
+                      plan buffers hold, the default); results are identical whatever the value,
+                      a small value runs the multi-chunk path on small problems */
 } boruta_opts;
 
 /* Host-side, caller-allocated outputs. */
@@ -225,6 +228,14 @@ int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacit
  *                        state once per node, partition traffic). */
 int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* launches, double* hist_bytes,
                                 double* split_ms, double* split_bytes);
+
+/* Timing of the last step's importance stage (Alg. 2 normalisation, or the
+ * Alg. 3 tree walks and their reduction), from CUDA events on the session's
+ * stream (0 when the step was replayed from a graph), and the number of
+ * node visits of the Alg. 3 walks: every node whose split test a walk
+ * applied, on the rows' own paths and on the re-walks with a feature's value
+ * swapped (0 for TreeImp).  Either pointer may be NULL. */
+int boruta_session_importance_stats(boruta_session* s, double* ms, double* node_visits);
 
 void boruta_session_destroy(boruta_session* s);
 

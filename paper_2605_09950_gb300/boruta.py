@@ -27,7 +27,8 @@ EXPORTS = [
     "boruta_batch_run",
     "boruta_batch_read", "boruta_batch_destroy", "boruta_session_create", "boruta_session_step",
     "boruta_session_read", "boruta_session_write", "boruta_session_dump",
-    "boruta_session_kernel_stats", "boruta_session_destroy", "boruta_philox", "boruta_perm",
+    "boruta_session_kernel_stats", "boruta_session_importance_stats", "boruta_session_destroy",
+    "boruta_philox", "boruta_perm",
     "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_quantise",
     "boruta_last_error",
 ]
@@ -42,7 +43,8 @@ class BorutaError(RuntimeError):
 class Opts(ct.Structure):
     _fields_ = [("stat", ct.c_int), ("precision", ct.c_int), ("tie_break", ct.c_int),
                 ("n_classes", ct.c_int), ("kl_eps", ct.c_double), ("stream", ct.c_void_p),
-                ("job", ct.c_uint32), ("host_inputs", ct.c_int), ("graph", ct.c_int), ("split_path", ct.c_int)]
+                ("job", ct.c_uint32), ("host_inputs", ct.c_int), ("graph", ct.c_int), ("split_path", ct.c_int),
+                ("chunk_nodes", ct.c_int)]
 
 
 class Job(ct.Structure):
@@ -89,6 +91,7 @@ def lib():
         L.boruta_session_kernel_stats.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int32),
                                                   ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                                   ct.POINTER(ct.c_double)]
+        L.boruta_session_importance_stats.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.boruta_session_destroy.argtypes = [vp]
         L.boruta_session_destroy.restype = None
         L.boruta_batch_create.argtypes = [ct.c_int, vp, vp, ct.POINTER(ct.c_void_p)]
@@ -124,11 +127,12 @@ def _stream():
 
 
 def make_opts(stat=0, precision=0, tie_break=0, n_classes=0, kl_eps=1e-7, job=0, host_inputs=0,
-              graph=0, split_path=0, stream=None) -> Opts:
+              graph=0, split_path=0, chunk_nodes=0, stream=None) -> Opts:
     o = Opts()
     lib().boruta_default_opts(ct.byref(o))
     o.stat, o.precision, o.tie_break, o.n_classes = stat, precision, tie_break, n_classes
     o.kl_eps, o.job, o.host_inputs, o.graph, o.split_path = kl_eps, job, host_inputs, graph, split_path
+    o.chunk_nodes = chunk_nodes
     o.stream = stream if stream is not None else (None if host_inputs else _stream())
     return o
 
@@ -294,6 +298,11 @@ class Session:
                                                  ct.byref(sb)))
         return dict(hist_ms=hms.value, launches=n.value, hist_bytes=hb.value, split_ms=sms.value,
                     split_bytes=sb.value)
+
+    def importance_stats(self):
+        ms, visits = ct.c_double(), ct.c_double()
+        _check(lib().boruta_session_importance_stats(self._h, ct.byref(ms), ct.byref(visits)))
+        return dict(ms=ms.value, node_visits=visits.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -56,7 +56,7 @@ struct boruta_session {
   Dev d{};
   cudaStream_t st = nullptr;
   int64_t p = 0, N = 0;
-  int task = 0, mtry_opt = 0, max_iter = 0, t = 0, split_path = 0;
+  int task = 0, mtry_opt = 0, max_iter = 0, t = 0, split_path = 0, chunk_nodes = 0;
   int pending_t = 0;  // iteration enqueued and not yet finished
   bool graph = false;                   // iterations replayed through an instantiated CUDA graph
   cudaStream_t gst = nullptr;           // capture stream of the graph
@@ -89,6 +89,8 @@ struct boruta_session {
   double split_bytes = 0.0;
   std::vector<cudaEvent_t> hev;  // around the histogram kernel of each level
   double hist_ms = 0.0, hist_bytes = 0.0;
+  cudaEvent_t iev[2] = {nullptr, nullptr};  // around the importance stage (Alg. 2 or 3)
+  double imp_ms = 0.0, imp_visits = 0.0;
 
   template <typename T>
   int alloc(T** p, size_t count) {
@@ -110,6 +112,8 @@ struct boruta_session {
     for (void* q : dev_allocs) cudaFree(q);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : hev) cudaEventDestroy(e);
+    for (cudaEvent_t e : iev)
+      if (e) cudaEventDestroy(e);
     if (st2) {
       cudaStreamSynchronize(st2);
       cudaStreamDestroy(st2);
@@ -144,6 +148,7 @@ static int check_args(const uint8_t* X, int64_t ld, const void* y, int64_t N, in
   if (o->n_classes < 0 || o->n_classes > kMaxClasses)
     return fail(BORUTA_EINVAL, "n_classes = %d outside [0, 8]", o->n_classes);
   if (o->split_path < 0 || o->split_path > 1) return fail(BORUTA_EINVAL, "opts: split_path takes 0 or 1");
+  if (o->chunk_nodes < 0) return fail(BORUTA_EINVAL, "opts: chunk_nodes must not be negative");
   if (o->precision < 0 || o->precision > 1 || o->tie_break < 0 || o->tie_break > 1 || o->stat < 0 ||
       o->stat > 1)
     return fail(BORUTA_EINVAL, "opts: precision, tie_break and stat take 0 or 1");
@@ -170,6 +175,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->task = task;
   s->mtry_opt = mtry;
   s->split_path = o->split_path;
+  s->chunk_nodes = o->chunk_nodes;
   s->graph = o->graph != 0;
   s->max_iter = max_iter;
   Dev& d = s->d;
@@ -381,6 +387,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   for (auto& e : s->ev) CK(cudaEventCreate(&e));
   s->hev.resize(2 * (max_depth + 1));
   for (auto& e : s->hev) CK(cudaEventCreate(&e));
+  for (auto& e : s->iev) CK(cudaEventCreate(&e));
   CK(cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking));
   if (s->graph) CK(cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
@@ -438,6 +445,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   d.nbands = 0;
   d.chunk0 = 0;
   d.chunk_cap = static_cast<uint32_t>(std::min<uint64_t>(d.item_cap / static_cast<uint64_t>(d.mtry), 1u << 26));
+  if (s->chunk_nodes > 0) d.chunk_cap = std::min<uint32_t>(d.chunk_cap, static_cast<uint32_t>(s->chunk_nodes));
   if (s->split_path == 0 && d.chunk_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
     int64_t w = std::max<int64_t>(1, kBandBytes / d.ldN);
     w = std::max<int64_t>(w, (p_aug + kMaxBands - 1) / kMaxBands);
@@ -483,11 +491,13 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
     launch_children(d, level, st);
     CK_LAUNCH("next-level kernels");
   }
+  if (timed) CK(cudaEventRecord(s->iev[0], st));
   if (d.permut)
     launch_permut(d, s->permut_grid, s->walk_grid, st);
   else
     launch_treeimp(d, s->tree_grid, st);
   CK_LAUNCH("importance kernels");
+  if (timed) CK(cudaEventRecord(s->iev[1], st));
   launch_stats_decide(d, st);
   CK_LAUNCH("k_stats / k_decide");
   CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -583,6 +593,13 @@ static int step_finish(boruta_session* s, int32_t* undecided) {
   s->split_launches = d.D;
   s->split_bytes = static_cast<double>(bytes[0]);
   s->hist_bytes = static_cast<double>(bytes[2]);
+  s->imp_ms = 0.0;
+  if (!s->graph) {
+    float ims = 0.f;
+    CK(cudaEventElapsedTime(&ims, s->iev[0], s->iev[1]));
+    s->imp_ms = ims;
+  }
+  s->imp_visits = static_cast<double>(bytes[3]);
   std::memcpy(s->state_h.data(), s->state_pin, s->p);
   s->t = t;
   const int32_t und = static_cast<int32_t>(s->status_h[1]);
@@ -644,6 +661,13 @@ int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* lau
   if (hist_bytes) *hist_bytes = s->hist_bytes;
   if (split_ms) *split_ms = s->split_ms;
   if (split_bytes) *split_bytes = s->split_bytes;
+  return 0;
+}
+
+int boruta_session_importance_stats(boruta_session* s, double* ms, double* node_visits) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  if (ms) *ms = s->imp_ms;
+  if (node_visits) *node_visits = s->imp_visits;
   return 0;
 }
 

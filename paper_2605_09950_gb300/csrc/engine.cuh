@@ -68,7 +68,8 @@ struct Dev {
   double* smax;                  // [max_iter]
   uint32_t* status;              // [0] error flags, [1] undecided count, [2] n_classes seen
   unsigned long long* counters;  // [0] split-stage algorithmic bytes, [1] max |y|,
-                                 // [2] histogram-kernel algorithmic bytes
+                                 // [2] histogram-kernel algorithmic bytes,
+                                 // [3] node visits of the Alg. 3 tree walks
 };
 
 constexpr int kScanBlocks = 512;

@@ -500,6 +500,7 @@ __device__ float loss32(const Dev& d, uint32_t q, uint32_t q2) {
 __global__ void __launch_bounds__(128) k_permut(Dev d) {
   const uint32_t chunks = (static_cast<uint32_t>(d.N) + 127u) / 128u;
   const uint64_t items = static_cast<uint64_t>(d.M) * chunks;
+  unsigned long long visits = 0;  // nodes whose test a walk applied (the base path and the re-walks)
   for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
     const int tau = static_cast<int>(item / chunks);
     const uint32_t noob = d.oob_cnt[tau];
@@ -529,6 +530,7 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
         c = right ? c1 : c0;
       }
       const uint32_t q = k;
+      visits += static_cast<unsigned long long>(depth);
       // the permuted row's bins of every feature on the path, loaded together
       uint8_t xq[kMaxDepth];
       for (int a = 0; a < depth; ++a) xq[a] = d.Xaug[static_cast<int64_t>(pw[a] >> 8) * d.ldN + pi];
@@ -583,6 +585,7 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
           for (int u = 0; u < kWalks; ++u) {
             if (ws[u] == kLeaf) continue;
             busy = true;
+            ++visits;
             const uint32_t fx = wfx[w0 + u];
             const uint32_t g = ws[u] >> 8;
             const uint8_t x = (g == (fx >> 8)) ? static_cast<uint8_t>(fx & 255u)
@@ -607,6 +610,9 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
       }
     }
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) visits += __shfl_xor_sync(kFull, visits, off);
+  if ((threadIdx.x & 31) == 0 && visits) atomicAdd(&d.counters[3], visits);
 }
 
 __global__ void k_permut_final(Dev d) {

@@ -59,9 +59,16 @@ def quantise(F: np.ndarray, n_bins: int) -> np.ndarray:
     rank = number of strictly smaller values in the column (ties share a bin)."""
     p, N = F.shape
     out = np.zeros((p, pad16(N)), dtype=np.uint8)
+    idx = np.arange(N)
     for j in range(p):
         col = F[j]
-        rank = np.searchsorted(np.sort(col), col, side="left")
+        order = np.argsort(col, kind="stable")
+        s = col[order]
+        start = np.empty(N, dtype=bool)  # first position of each run of equal values
+        start[0] = True
+        np.not_equal(s[1:], s[:-1], out=start[1:])
+        rank = np.empty(N, dtype=np.int64)
+        rank[order] = np.maximum.accumulate(np.where(start, idx, 0))
         out[j, :N] = np.minimum(n_bins - 1, (n_bins * rank) // N).astype(np.uint8)
     return out
 
@@ -130,22 +137,26 @@ def snp_regression(N=20_000, p=20_000, n_add=30, n_pairs=10, seed=2, n_trees=256
 
 
 def multiclass_toeplitz(N=1_000_000, p=500, block=10, n_inf=25, n_classes=5, seed=5, n_trees=300,
-                        max_depth=20, max_iter=60, n_bins=256, importance=PERMUT) -> Workload:
-    """Large-N multiclass: p columns in blocks of 10 with AR(1) correlation
-    0.8 inside each block (Toeplitz 0.8^|i-j|), 5 classes drawn from a
-    softmax over the first column of the first 25 blocks."""
+                        max_depth=20, max_iter=60, n_bins=256, importance=PERMUT, quantiser=None) -> Workload:
+    """Large-N multiclass: p float32 columns in blocks of 10 with AR(1)
+    correlation 0.8 inside each block (Toeplitz 0.8^|i-j|), 5 classes drawn
+    from a softmax over the first column of the first 25 blocks.
+    quantiser(F, n_bins) bins the float32 (p, N) features (default: the
+    numpy statement of the rank rule, `quantise`)."""
     rng = np.random.default_rng(np.random.PCG64(seed))
     inf = np.arange(n_inf) * block
     W = rng.normal(0.0, 1.0 / math.sqrt(n_inf), size=(n_classes, n_inf))
-    X = np.zeros((p, pad16(N)), dtype=np.uint8)
+    F = np.empty((p, N), dtype=np.float32)
     logits = np.zeros((n_classes, N))
     col = None
-    for j in range(p):  # column by column: AR(1) inside each block, quantised at once
+    for j in range(p):  # column by column: AR(1) inside each block
         z = rng.standard_normal(N)
         col = z if j % block == 0 else 0.8 * col + 0.6 * z
         if j % block == 0 and j // block < n_inf:
             logits += np.outer(W[:, j // block], col)
-        X[j] = quantise(col[None, :], n_bins)[0]
+        F[j] = col
+    X = (quantiser or quantise)(F, n_bins)
+    del F
     logits -= logits.max(axis=0)
     P = np.exp(logits)
     P /= P.sum(axis=0)
@@ -156,10 +167,11 @@ def multiclass_toeplitz(N=1_000_000, p=500, block=10, n_inf=25, n_classes=5, see
 
 
 def batch_jobs(n_jobs=64, seed=4, n_trees=200, max_depth=10, max_iter=50, n_bins=128,
-               N_range=(500, 50_000), p_range=(20, 5000)) -> list[Workload]:
+               N_range=(500, 50_000), p_range=(20, 5000), quantiser=None) -> list[Workload]:
     """Independent classification problems of uneven size: N and p
-    log-uniform, 2-4 classes, 10% informative columns with per-class mean
-    shifts 0.8 * Bernoulli(1/2) (class 0 at 0)."""
+    log-uniform, 2-4 classes, 10% informative float32 columns with per-class
+    mean shifts 0.8 * Bernoulli(1/2) (class 0 at 0).  quantiser as for
+    multiclass_toeplitz."""
     rng = np.random.default_rng(np.random.PCG64(seed))
     jobs = []
     for j in range(n_jobs):
@@ -173,7 +185,7 @@ def batch_jobs(n_jobs=64, seed=4, n_trees=200, max_depth=10, max_iter=50, n_bins
             mu = 0.8 * (rng.random(C) < 0.5)
             mu[0] = 0.0
             F[col] += mu[y]
-        jobs.append(Workload(f"job{j}_N{N}_p{p}_C{C}", quantise(F, n_bins), y, N, p,
+        jobs.append(Workload(f"job{j}_N{N}_p{p}_C{C}", (quantiser or quantise)(F.astype(np.float32), n_bins), y, N, p,
                              CLASSIFICATION | PERMUT, C, n_bins, n_trees, max_depth, max_iter,
                              seed=seed * 1000 + j, informative=inf))
     return jobs

@@ -29,6 +29,24 @@ def test_header_and_binding_agree():
     assert declared_functions() == sorted(boruta.EXPORTS)
 
 
+def _struct_fields(name):
+    text = open(os.path.join(ROOT, "include", "boruta.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", text).group(1)
+    return [re.findall(r"(\w+)(?:\[\w*\])?\s*$", decl.strip())[0]
+            for stmt in body.split(";") if stmt.strip() for decl in stmt.split(",")
+            if re.findall(r"(\w+)(?:\[\w*\])?\s*$", decl.strip())]
+
+
+@pytest.mark.parametrize("cname,pyname", [("boruta_opts", "Opts"), ("boruta_result", "Result"),
+                                          ("boruta_job", "Job")])
+def test_binding_structs_follow_the_header(cname, pyname):
+    """The ctypes structures list the header's fields in the header's order."""
+    from paper_2605_09950_gb300 import boruta
+
+    assert [f for f, _ in getattr(boruta, pyname)._fields_] == _struct_fields(cname)
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name

@@ -291,15 +291,39 @@ def test_checkpoint_resume_is_exact():
 
 # ---------------------------------------------------------------- full size, sampled
 
-def test_binary_n100000_p1000_sampled():
-    """Binary N=1e5, p=1000, 500 trees, depth 16 (one iteration, in the
-    launch configuration the benchmark times): trees 0 and 499 node by node
-    and their Permut rows against the oracle; properties of every tree."""
+def _oracle_trees(P, t, live, sha, taus, **what):
+    """Oracle trees on host threads (the oracle's C releases the GIL and
+    keeps no global state)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=len(taus)) as ex:
+        return list(ex.map(lambda tau: P.tree(t, live, sha, tau, **what), taus))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_binary_n100000_p1000_sampled(precision):
+    """Binary N=1e5, p=1000, 500 trees, depth 16, in both precision forms
+    (one iteration, in the launch configuration the benchmark times): trees
+    0 and 499 node by node and their Permut rows against the oracle (FP64
+    terms within 1e-12, FP32 terms within 1e-5); properties of every tree."""
     from paper_2605_09950_gb300 import boruta
 
     w = synth.binary_wide(max_iter=3)
-    S, P, st, imp = check_iteration(w, trees=[0, 499])
+    S = session(w, precision=precision)
+    S.step()
+    P = oracle_problem(w)
+    live = np.arange(w.p, dtype=np.int32)
+    sha = P.shadow(1, live)
+    np.testing.assert_array_equal(S.dump(boruta.DUMP_SHADOW, np.uint8).reshape(sha.shape), sha)
+    nodes = S.dump(boruta.DUMP_NODES, boruta.NODE_DTYPE)
+    ptr = S.dump(boruta.DUMP_TREE_PTR, np.int64)
+    imp = S.dump(boruta.DUMP_IMP, np.float64).reshape(w.n_trees, -1)
     boot = S.dump(boruta.DUMP_BOOT, np.uint32).reshape(w.n_trees, w.N)
+    taus = [0, w.n_trees - 1]
+    for tau, (nd, _, pm) in zip(taus, _oracle_trees(P, 1, live, sha, taus, permut=True)):
+        np.testing.assert_array_equal(boot[tau], oracle.bootstrap(w.seed, 0, 1, tau, w.N))
+        compare_nodes(nodes[ptr[tau]:ptr[tau + 1]], nd, exact_delta=precision == 0)
+        close(imp[tau], pm, REL64 if precision == 0 else REL32)
     assert (boot.sum(axis=1) == w.N).all()
     assert np.isfinite(imp).all() and (imp >= -1e-15).all()
 
@@ -320,27 +344,33 @@ def test_grouped_item_path(case):
     check_iteration(w, split_path=1)
 
 
-# ---------------------------------------------------------------- full-size workloads, sampled
-
-def _top_levels(S, P, t, live, sha, trees, L, exact_delta=True):
-    """Nodes above depth L do not depend on what happens below it: the GPU
-    tree's top L levels must equal the oracle tree built with max_depth = L."""
+@pytest.mark.parametrize("case", ["binary", "multiclass", "regression"])
+def test_band_path_in_many_chunks(case):
+    """The band path runs a level's larger nodes in chunks that fit its plan
+    buffers (at full size: SNP regression from about depth 6, multiclass
+    N=1e6 at depths 17-19).  opts.chunk_nodes = 3 forces several chunks per
+    level on small problems: trees and importances against the oracle, and
+    the same dumps as the one-chunk run."""
     from paper_2605_09950_gb300 import boruta
 
-    nodes = S.dump(boruta.DUMP_NODES, boruta.NODE_DTYPE)
-    ptr = S.dump(boruta.DUMP_TREE_PTR, np.int64)
-    saved = P.c.max_depth
-    P.c.max_depth = L
-    try:
-        for tau in trees:
-            nd, _, _ = P.tree(t, live, sha, tau)
-            g = nodes[ptr[tau]:ptr[tau + 1]]
-            g, o = g[g["depth"] < L], nd[nd["depth"] < L]
-            compare_nodes(g, o, exact_delta=exact_delta)
-    finally:
-        P.c.max_depth = saved
-    return nodes, ptr
+    if case == "binary":
+        w = synth.binary_small(N=900, p=20, n_inf=4, n_trees=8, max_depth=9, max_iter=3, importance=2)
+    elif case == "multiclass":
+        w = synth.multiclass_toeplitz(N=3000, p=20, block=5, n_inf=3, n_classes=4, n_trees=6, max_depth=8,
+                                      max_iter=3, importance=2)
+    else:
+        w = synth.snp_regression(N=900, p=40, n_add=5, n_pairs=2, n_trees=6, max_depth=7, max_iter=3)
+    S, _, _, imp = check_iteration(w, chunk_nodes=3)
+    ref = session(w)
+    ref.step()
+    for what, dt in ((boruta.DUMP_NODES, boruta.NODE_DTYPE), (boruta.DUMP_IMP, np.float64),
+                     (boruta.DUMP_STAT, np.float64)):
+        np.testing.assert_array_equal(S.dump(what, dt), ref.dump(what, dt))
+    levels = S.dump(boruta.DUMP_LEVELS, np.float64).reshape(-1, 3)
+    assert levels[:, 0].max() > 3 * 3  # some level held more than three chunks of nodes
 
+
+# ---------------------------------------------------------------- full-size workloads, sampled
 
 def _importance_properties(S, nodes, ptr, n_trees, permut):
     from paper_2605_09950_gb300 import boruta
@@ -356,11 +386,12 @@ def _importance_properties(S, nodes, ptr, n_trees, permut):
             assert imp[tau].sum() == pytest.approx(1.0, abs=1e-12)
 
 
-def test_snp_regression_n20000_p20000_sampled():
+def test_snp_regression_n20000_p20000_whole_trees():
     """SNP regression N=2e4, p=2e4 (40,000 augmented columns, mtry 13,333),
-    256 trees, depth 12, TreeImp: every shadow column, two bootstrap rows and
-    the top three levels of two trees against the oracle; importance
-    properties of every tree."""
+    256 trees, depth 12, TreeImp (its levels run the band path in several
+    chunks from about depth 6): every shadow column, two bootstrap rows, and
+    two whole trees node by node with their TreeImp rows (bit-exact) against
+    the oracle; importance properties of every tree."""
     from paper_2605_09950_gb300 import boruta
 
     w = synth.snp_regression(max_iter=3)
@@ -371,16 +402,24 @@ def test_snp_regression_n20000_p20000_sampled():
     sha = P.shadow(1, live)
     np.testing.assert_array_equal(S.dump(boruta.DUMP_SHADOW, np.uint8).reshape(sha.shape), sha)
     boot = S.dump(boruta.DUMP_BOOT, np.uint32).reshape(w.n_trees, w.N)
-    for tau in (0, w.n_trees - 1):
+    nodes = S.dump(boruta.DUMP_NODES, boruta.NODE_DTYPE)
+    ptr = S.dump(boruta.DUMP_TREE_PTR, np.int64)
+    imp = S.dump(boruta.DUMP_IMP, np.float64).reshape(w.n_trees, -1)
+    taus = [0, w.n_trees - 1]
+    for tau, (nd, ti, _) in zip(taus, _oracle_trees(P, 1, live, sha, taus, treeimp=True)):
         np.testing.assert_array_equal(boot[tau], oracle.bootstrap(w.seed, 0, 1, tau, w.N))
-    nodes, ptr = _top_levels(S, P, 1, live, sha, [0, w.n_trees - 1], L=3)
+        compare_nodes(nodes[ptr[tau]:ptr[tau + 1]], nd)
+        np.testing.assert_array_equal(imp[tau], ti)
     _importance_properties(S, nodes, ptr, w.n_trees, permut=False)
 
 
-def test_multiclass_n1000000_p500_sampled():
+def test_multiclass_n1000000_p500_whole_trees():
     """Five classes, N=1e6, p=500 (Toeplitz blocks), 300 trees, depth 20,
-    Permut: shadows, two bootstrap rows and the top six levels of two trees
-    against the oracle; importance properties of every tree."""
+    Permut in the FP32-term form the benchmark times (its deepest levels run
+    the band path in several chunks): shadows, two bootstrap rows and two
+    whole trees node by node against the oracle (split deltas within 1e-5);
+    importance properties of every tree.  (An oracle Permut row of this size
+    takes minutes; the rows' arithmetic is checked on the smaller cases.)"""
     from paper_2605_09950_gb300 import boruta
 
     w = synth.multiclass_toeplitz(max_iter=3)
@@ -391,7 +430,10 @@ def test_multiclass_n1000000_p500_sampled():
     sha = P.shadow(1, live)
     np.testing.assert_array_equal(S.dump(boruta.DUMP_SHADOW, np.uint8).reshape(sha.shape), sha)
     boot = S.dump(boruta.DUMP_BOOT, np.uint32).reshape(w.n_trees, w.N)
-    for tau in (0, w.n_trees - 1):
+    nodes = S.dump(boruta.DUMP_NODES, boruta.NODE_DTYPE)
+    ptr = S.dump(boruta.DUMP_TREE_PTR, np.int64)
+    taus = [0, w.n_trees - 1]
+    for tau, (nd, _, _) in zip(taus, _oracle_trees(P, 1, live, sha, taus)):
         np.testing.assert_array_equal(boot[tau], oracle.bootstrap(w.seed, 0, 1, tau, w.N))
-    nodes, ptr = _top_levels(S, P, 1, live, sha, [0, w.n_trees - 1], L=6, exact_delta=False)  # FP32 form
+        compare_nodes(nodes[ptr[tau]:ptr[tau + 1]], nd, exact_delta=False)
     _importance_properties(S, nodes, ptr, w.n_trees, permut=True)

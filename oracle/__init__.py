@@ -48,7 +48,7 @@ class Problem(ct.Structure):
         ("N", ct.c_int64), ("p", ct.c_int64), ("task", ct.c_int), ("n_classes", ct.c_int),
         ("n_trees", ct.c_int), ("max_depth", ct.c_int), ("mtry", ct.c_int), ("n_bins", ct.c_int),
         ("max_iter", ct.c_int), ("alpha", ct.c_double), ("seed", ct.c_uint64), ("job", ct.c_uint32),
-        ("stat", ct.c_int), ("kl_eps", ct.c_double), ("tie_break", ct.c_int),
+        ("stat", ct.c_int), ("kl_eps", ct.c_double), ("tie_break", ct.c_int), ("permut_form", ct.c_int),
     ]
 
 
@@ -94,6 +94,8 @@ def lib():
             L.orc_tree.argtypes = [P(Problem), ct.c_int, vp, ct.c_int64, vp, ct.c_int, vp, ct.c_int64,
                                    P(ct.c_int64), vp, vp]
             L.orc_tree.restype = ct.c_int
+            L.orc_forest_permut.argtypes = [P(Problem), ct.c_int, vp, ct.c_int64, vp, vp]
+            L.orc_forest_permut.restype = ct.c_int
             L.orc_decide.argtypes = [ct.c_int, ct.c_double, ct.c_int64, vp, vp]
             L.orc_iteration.argtypes = [P(Problem), ct.c_int, vp, vp, vp, P(ct.c_double), vp, vp,
                                         P(ct.c_int64)]
@@ -212,7 +214,7 @@ class BorutaProblem:
     """
 
     def __init__(self, X, y, task, n_trees, max_depth, n_bins, max_iter, alpha=0.01, seed=0,
-                 mtry=0, n_classes=0, job=0, stat=0, kl_eps=1e-7, tie_break=0, N=None):
+                 mtry=0, n_classes=0, job=0, stat=0, kl_eps=1e-7, tie_break=0, permut_form=0, N=None):
         self.X = np.ascontiguousarray(X, dtype=np.uint8)
         self.N = int(N if N is not None else self.X.shape[1])
         self.p = int(self.X.shape[0])
@@ -231,7 +233,7 @@ class BorutaProblem:
             yreg=self.y.ctypes.data if (task & 1) == 1 else None,
             N=self.N, p=self.p, task=self.task, n_classes=self.n_classes, n_trees=n_trees,
             max_depth=max_depth, mtry=mtry, n_bins=n_bins, max_iter=max_iter, alpha=alpha,
-            seed=seed, job=job, stat=stat, kl_eps=kl_eps, tie_break=tie_break)
+            seed=seed, job=job, stat=stat, kl_eps=kl_eps, tie_break=tie_break, permut_form=permut_form)
 
     @property
     def n_trees(self):
@@ -267,6 +269,17 @@ class BorutaProblem:
             raise RuntimeError(f"oracle tree failed ({rc})")
         return (nd[: nn.value] if nodes else None), ti, pm
 
+    def forest_permut(self, t, live, Xsha):
+        """Alg. 3 as printed (every row, the forest's prediction): one
+        importance per augmented column."""
+        live = np.ascontiguousarray(live, dtype=np.int32)
+        Xsha = np.ascontiguousarray(Xsha, dtype=np.uint8)
+        imp = np.zeros(live.size + Xsha.shape[0])
+        rc = lib().orc_forest_permut(ct.byref(self.c), t, _ptr(live), live.size, _ptr(Xsha), _ptr(imp))
+        if rc:
+            raise RuntimeError(f"oracle forest failed ({rc})")
+        return imp
+
     def iteration(self, t, state, hits):
         """One Alg. 1 loop body; returns dict with the updated state and dumps."""
         state = np.array(state, dtype=np.int8)
@@ -275,6 +288,7 @@ class BorutaProblem:
         p_aug = p_live + shadow_count(p_live)
         hist = np.zeros(self.p)
         smax = ct.c_double()
+        rows = 1 if (self.task & PERMUT and self.c.permut_form == 1) else self.n_trees
         imp = np.zeros((self.n_trees, p_aug))
         s = np.zeros(p_aug)
         pa = ct.c_int64()
@@ -282,7 +296,7 @@ class BorutaProblem:
                                  ct.byref(smax), _ptr(imp), _ptr(s), ct.byref(pa))
         if rc:
             raise RuntimeError(f"oracle iteration failed ({rc})")
-        return dict(state=state, hits=hits, hist=hist, shadow_max=smax.value, imp=imp, s=s)
+        return dict(state=state, hits=hits, hist=hist, shadow_max=smax.value, imp=imp[:rows], s=s)
 
     def run(self):
         p, T = self.p, self.c.max_iter

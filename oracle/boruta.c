@@ -5,7 +5,8 @@
  *   X_cur = columns with state >= 0 (undecided and accepted), in order;
  *   X_sha = shuffled copies of X_cur, doubled until >= 5 columns;
  *   fit a forest on [X_cur || X_sha]; per-tree importance rows (Alg. 2 or
- *   the OOB form of Alg. 3);
+ *   the OOB form of Alg. 3), or one row for the whole forest (Alg. 3 as
+ *   printed, permut_form = 1: that row is the hit statistic s);
  *   hit statistic per augmented column over the trees (FP64):
  *       mean_j = (sum_tau imp[tau][j]) / M
  *       sd_j   = sqrt(sum_tau (imp[tau][j] - mean_j)^2 / (M - 1))   (0 if M = 1)
@@ -61,12 +62,18 @@ int orc_iteration(const orc_problem* P, int t, int8_t* state, int32_t* hits, dou
   orc_shadow(P, t, live, p_live, Xsha);
 
   int permut = (P->task & ORC_PERMUT) != 0;
+  int forest = permut && P->permut_form == 1; /* Alg. 3 as printed: one importance row */
   double* imp = (double*)malloc(sizeof(double) * (size_t)(M * p_aug));
   int rc = 0;
-  for (int64_t tau = 0; tau < M && rc == 0; tau++) {
-    double* row = imp + tau * p_aug;
-    rc = orc_tree(P, t, live, p_live, Xsha, (int)tau, NULL, 0, NULL, permut ? NULL : row,
-                  permut ? row : NULL);
+  if (forest) {
+    rc = orc_forest_permut(P, t, live, p_live, Xsha, imp);
+    M = 1; /* the statistic is that row itself */
+  } else {
+    for (int64_t tau = 0; tau < M && rc == 0; tau++) {
+      double* row = imp + tau * p_aug;
+      rc = orc_tree(P, t, live, p_live, Xsha, (int)tau, NULL, 0, NULL, permut ? NULL : row,
+                    permut ? row : NULL);
+    }
   }
   free(Xsha);
   if (rc) {
@@ -92,7 +99,7 @@ int orc_iteration(const orc_problem* P, int t, int8_t* state, int32_t* hits, dou
       z = (mean == 0.0) ? 0.0 : INFINITY;
     else
       z = mean / (sd / sqrt((double)M));
-    s[j] = (P->stat == 1) ? mean : z;
+    s[j] = (P->stat == 1 || forest) ? mean : z;
   }
   free(sq);
 

@@ -308,38 +308,43 @@ static int cmp_node_level(const void* a, const void* b) {
   return (x->heap > y->heap) - (x->heap < y->heap);
 }
 
-int orc_tree(const orc_problem* P, int t, const int32_t* live, int64_t p_live,
-             const uint8_t* Xsha, int tree, orc_node* nodes_out, int64_t cap, int64_t* n_nodes,
-             double* imp_treeimp, double* imp_permut) {
-  int64_t N = P->N;
+/* Column pointers of the augmented matrix [X_cur || X_sha]. */
+static const uint8_t** aug_columns(const orc_problem* P, const int32_t* live, int64_t p_live,
+                                   const uint8_t* Xsha, int64_t* p_aug) {
   int64_t n_sha = orc_shadow_count(p_live);
-  int64_t p_aug = p_live + n_sha;
-  const uint8_t** col = (const uint8_t**)malloc(sizeof(uint8_t*) * (size_t)p_aug);
+  *p_aug = p_live + n_sha;
+  const uint8_t** col = (const uint8_t**)malloc(sizeof(uint8_t*) * (size_t)*p_aug);
   for (int64_t a = 0; a < p_live; a++) col[a] = P->X + (int64_t)live[a] * P->ld;
-  for (int64_t c = 0; c < n_sha; c++) col[p_live + c] = Xsha + c * N;
+  for (int64_t c = 0; c < n_sha; c++) col[p_live + c] = Xsha + c * P->N;
+  return col;
+}
 
-  tree_t T;
-  memset(&T, 0, sizeof T);
-  T.P = P;
-  T.d.kind = P->task & 1;
-  T.d.C = (T.d.kind == ORC_CLASSIFICATION) ? P->n_classes : 1;
-  T.d.B = P->n_bins;
-  T.d.ycls = P->ycls;
-  T.d.yreg = P->yreg;
-  T.d.col = col;
-  T.t = t;
-  T.tree = tree;
-  T.D = P->max_depth;
-  T.p_aug = p_aug;
-  T.mtry = (int)(P->mtry > 0 ? (P->mtry < p_aug ? P->mtry : p_aug)
-                             : orc_default_mtry(P->task, p_aug));
-  T.cap = 2 * N + 1;
-  T.nodes = (orc_node*)malloc(sizeof(orc_node) * (size_t)T.cap);
-  T.left = (int64_t*)malloc(sizeof(int64_t) * (size_t)T.cap);
-  T.right = (int64_t*)malloc(sizeof(int64_t) * (size_t)T.cap);
+/* Fits tree `tree` of iteration t: bootstrap (counts into cnt[N]), then the
+ * recursive growth from the root.  Returns 0, or -1 / -2 (pool / 256-bit
+ * bound); the caller frees the tree with tree_free. */
+static int tree_fit(tree_t* T, const orc_problem* P, int t, int tree, const uint8_t** col,
+                    int64_t p_aug, uint32_t* cnt) {
+  int64_t N = P->N;
+  memset(T, 0, sizeof *T);
+  T->P = P;
+  T->d.kind = P->task & 1;
+  T->d.C = (T->d.kind == ORC_CLASSIFICATION) ? P->n_classes : 1;
+  T->d.B = P->n_bins;
+  T->d.ycls = P->ycls;
+  T->d.yreg = P->yreg;
+  T->d.col = col;
+  T->t = t;
+  T->tree = tree;
+  T->D = P->max_depth;
+  T->p_aug = p_aug;
+  T->mtry = (int)(P->mtry > 0 ? (P->mtry < p_aug ? P->mtry : p_aug)
+                              : orc_default_mtry(P->task, p_aug));
+  T->cap = 2 * N + 1;
+  T->nodes = (orc_node*)malloc(sizeof(orc_node) * (size_t)T->cap);
+  T->left = (int64_t*)malloc(sizeof(int64_t) * (size_t)T->cap);
+  T->right = (int64_t*)malloc(sizeof(int64_t) * (size_t)T->cap);
 
   /* bootstrap: in-bag rows ascending with their draw counts */
-  uint32_t* cnt = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
   orc_bootstrap(P->seed, P->job, t, tree, N, cnt);
   uint32_t* rows = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
   uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
@@ -350,8 +355,27 @@ int orc_tree(const orc_problem* P, int t, const int32_t* live, int64_t p_live,
       w[nin] = cnt[i];
       nin++;
     }
-  grow(&T, 0, 0, rows, w, nin);
-  int rc = T.err ? -1 : (T.of ? -2 : 0);
+  grow(T, 0, 0, rows, w, nin);
+  free(rows);
+  free(w);
+  return T->err ? -1 : (T->of ? -2 : 0);
+}
+
+static void tree_free(tree_t* T) {
+  free(T->nodes);
+  free(T->left);
+  free(T->right);
+}
+
+int orc_tree(const orc_problem* P, int t, const int32_t* live, int64_t p_live,
+             const uint8_t* Xsha, int tree, orc_node* nodes_out, int64_t cap, int64_t* n_nodes,
+             double* imp_treeimp, double* imp_permut) {
+  int64_t N = P->N;
+  int64_t p_aug;
+  const uint8_t** col = aug_columns(P, live, p_live, Xsha, &p_aug);
+  tree_t T;
+  uint32_t* cnt = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+  int rc = tree_fit(&T, P, t, tree, col, p_aug, cnt);
 
   /* Alg. 2: per tree, gain x samples summed per feature, then divided by
    * the tree's total.  Sums are exact, rounded once. */
@@ -420,11 +444,95 @@ int orc_tree(const orc_problem* P, int t, const int32_t* live, int64_t p_live,
   }
   if (n_nodes) *n_nodes = T.n;
   free(cnt);
-  free(rows);
-  free(w);
-  free(T.nodes);
-  free(T.left);
-  free(T.right);
+  tree_free(&T);
+  free(col);
+  return rc;
+}
+
+/* ---------------- Alg. 3 as printed: every row, the forest's prediction ----------------
+ *
+ * The model is the whole forest: its prediction for a row is the mean over
+ * the M trees of the leaf's value -- the class fractions c_k/n of the leaf
+ * (predicted class probabilities) or the leaf mean S/n (regression, units of
+ * 2^-20).  y_gpu is the forest's prediction for every row of
+ * [X_cur || X_sha]; for each augmented column f, that column is replaced by
+ * its values at flush_index (one permutation of the N rows per iteration,
+ * shared by all columns), every row is predicted again, and imp[f] is the
+ * mean over the N rows of the loss between the two predictions: the squared
+ * difference in real units (regression), or KL(P~_base || P~_perm) of the
+ * smoothed class probabilities P~_k = (P_k + eps) / (1 + C eps).
+ * Each mean over trees is the exact sum of the per-tree doubles rounded
+ * once, then divided by M; the mean over rows is exact, rounded once. */
+
+static double leaf_value(const tree_t* T, int64_t q, int k) {
+  const orc_node* nd = &T->nodes[q];
+  return (double)nd->stat[k] / (double)nd->n;
+}
+
+static double forest_loss(const orc_problem* P, int kind, int C, const double* a, const double* b) {
+  if (kind == ORC_REGRESSION) {
+    double diff = (a[0] - b[0]) * 0x1p-20;
+    return diff * diff;
+  }
+  double eps = P->kl_eps;
+  double norm = 1.0 + (double)C * eps;
+  double kl = 0.0;
+  for (int k = 0; k < C; k++) {
+    double pa = (a[k] + eps) / norm;
+    double pb = (b[k] + eps) / norm;
+    kl += pa * log(pa / pb);
+  }
+  return kl;
+}
+
+int orc_forest_permut(const orc_problem* P, int t, const int32_t* live, int64_t p_live,
+                      const uint8_t* Xsha, double* imp) {
+  int64_t N = P->N, M = P->n_trees;
+  int64_t p_aug;
+  const uint8_t** col = aug_columns(P, live, p_live, Xsha, &p_aug);
+  tree_t* T = (tree_t*)calloc((size_t)M, sizeof(tree_t));
+  uint32_t* cnt = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+  int rc = 0;
+  int64_t built = 0;
+  for (; built < M && rc == 0; built++) rc = tree_fit(&T[built], P, t, (int)built, col, p_aug, cnt);
+  free(cnt);
+  if (rc == 0) {
+    int kind = P->task & 1;
+    int K = kind == ORC_CLASSIFICATION ? P->n_classes : 1;
+    uint64_t* pi = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)N);
+    orc_permut_table(P, t, pi);
+    double* vals = (double*)malloc(sizeof(double) * (size_t)M);
+    double* base = (double*)malloc(sizeof(double) * (size_t)(N * K));
+    double* perm = (double*)malloc(sizeof(double) * (size_t)K);
+    double* L = (double*)malloc(sizeof(double) * (size_t)N);
+    int64_t* leaf = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
+    for (int64_t i = 0; i < N; i++) { /* y_gpu: the forest's own prediction */
+      for (int64_t tau = 0; tau < M; tau++) leaf[tau] = predict(&T[tau], (uint32_t)i, -1, 0);
+      for (int k = 0; k < K; k++) {
+        for (int64_t tau = 0; tau < M; tau++) vals[tau] = leaf_value(&T[tau], leaf[tau], k);
+        base[i * K + k] = exact_sum(vals, M, 1) / (double)M;
+      }
+    }
+    for (int64_t f = 0; f < p_aug; f++) {
+      for (int64_t i = 0; i < N; i++) { /* column f read at flush_index[i] */
+        for (int64_t tau = 0; tau < M; tau++) leaf[tau] = predict(&T[tau], (uint32_t)i, f, (uint32_t)pi[i]);
+        for (int k = 0; k < K; k++) {
+          for (int64_t tau = 0; tau < M; tau++) vals[tau] = leaf_value(&T[tau], leaf[tau], k);
+          perm[k] = exact_sum(vals, M, 1) / (double)M;
+        }
+        L[i] = forest_loss(P, kind, K, base + i * K, perm);
+      }
+      imp[f] = exact_sum(L, N, 1) / (double)N;
+    }
+    free(pi);
+    free(vals);
+    free(base);
+    free(perm);
+    free(L);
+    free(leaf);
+  }
+  for (int64_t tau = 0; tau < built; tau++) tree_free(&T[tau]);
+  free(T);
   free(col);
   return rc;
 }

@@ -60,6 +60,9 @@ typedef struct {
   int stat;             /* 0 = Z score (mean / (sd / sqrt(M))), 1 = mean */
   double kl_eps;        /* smoothing of class probabilities in the KL loss */
   int tie_break;        /* equal scores: 0 = lowest feature index, 1 = first drawn feature; then lowest bin */
+  int permut_form;      /* Alg. 3 rows: 0 = each tree's OOB rows against that tree's prediction,
+                           1 = every row against the forest's prediction (the printed algorithm;
+                           one importance per column, which is then the hit statistic) */
 } orc_problem;
 
 /* One tree node, as dumped for parity checks.  Trees are listed in
@@ -120,6 +123,12 @@ int orc_tree(const orc_problem* P, int t, const int32_t* live, int64_t p_live,
              const uint8_t* Xsha, int tree, orc_node* nodes, int64_t cap,
              int64_t* n_nodes, double* imp_treeimp, double* imp_permut);
 
+/* ---- Alg. 3 as printed: all N rows, the forest's averaged prediction ----
+ * imp[p_aug]: mean over rows of the loss between the forest's prediction and
+ * its prediction with column f read at flush_index (see forest.c). */
+int orc_forest_permut(const orc_problem* P, int t, const int32_t* live, int64_t p_live,
+                      const uint8_t* Xsha, double* imp);
+
 /* ---- the test of Alg. 1 alone ----
  * state[p] (1 accepted, 0 undecided, -1 rejected) is updated in place from
  * the hit counts after iteration t. */
@@ -128,7 +137,7 @@ void orc_decide(int t, double alpha, int64_t p, const int32_t* hits, int8_t* sta
 /* ---- one Boruta iteration (Alg. 1 loop body) ----
  * state/hits are updated in place; hist_row[p] receives the hit statistic of
  * each live feature (NaN otherwise); imp (n_trees x p_aug) and s (p_aug) are
- * optional dumps. */
+ * optional dumps (with permut_form = 1, imp holds one row of p_aug). */
 int orc_iteration(const orc_problem* P, int t, int8_t* state, int32_t* hits,
                   double* hist_row, double* shadow_max, double* imp, double* s,
                   int64_t* p_aug_out);

@@ -529,6 +529,147 @@ def test_permut_multiclass_stump_kl(C):
     assert np.count_nonzero(pm) == 1
 
 
+# ---------------------------------------------------------------- Alg. 3 as printed
+
+def _stump_forest(task, C, M=2, N=500, p=5, B=8, seed=21):
+    """M depth-1 trees on raw seeded data (as _stump); returns the problem,
+    its augmented columns, live set, shadow matrix, the trees' (feature, bin)
+    and bootstrap counts, flush_index and the raw targets."""
+    rng = np.random.default_rng(seed)
+    X = np.zeros((p, synth.pad16(N)), np.uint8)
+    X[:, :N] = rng.integers(0, B, size=(p, N))
+    if task & 1:
+        y = (rng.standard_normal(N) * 2**20 + X[0, :N].astype(np.int64) * 2**19
+             - X[1, :N].astype(np.int64) * 2**18).astype(np.int64)
+    else:
+        y = ((rng.integers(0, C, size=N) + (X[0, :N] >= B // 2) + (X[1, :N] >= B // 2)) % C).astype(np.uint8)
+    P = oracle.BorutaProblem(X, y, task | 2, n_trees=M, max_depth=1, n_bins=B, max_iter=1, seed=seed,
+                             n_classes=C if task == 0 else 0, permut_form=1, N=N)
+    live = np.arange(p, dtype=np.int32)
+    sha = P.shadow(1, live)
+    cols = np.concatenate([X[:, :N], sha])
+    splits, cnts = [], []
+    for tau in range(M):
+        nodes, _, _ = P.tree(1, live, sha, tau)
+        assert nodes[0]["feature"] >= 0
+        splits.append((int(nodes[0]["feature"]), int(nodes[0]["bin"])))
+        cnts.append(oracle.bootstrap(seed, 0, 1, tau, N))
+    return P, cols, live, sha, splits, cnts, P.permut_table(1), y[:N]
+
+
+def _forest_pred(cols, splits, leafval, i, f=None, pi_i=None):
+    """Mean over trees of the leaf value reached by row i (column f read at
+    row pi_i), in exact rationals."""
+    total = Fraction(0)
+    for tau, (g, b) in enumerate(splits):
+        v = cols[g][pi_i] if g == f else cols[g][i]
+        total += leafval[tau][bool(v <= b)]
+    return total / len(splits)
+
+
+def test_forest_permut_regression_two_stumps_exact():
+    """Alg. 3 as printed, regression: the model is the forest (the mean of
+    the trees' leaf means), the rows are all N rows, and imp[f] is the mean
+    squared difference between the forest's prediction and its prediction
+    with column f read at flush_index -- recomputed here in exact rationals
+    from the raw targets for a forest of two stumps.  Columns that no tree
+    splits on get exactly 0.  (Checked to fail when the forest mean drops
+    its 1/M, when the mean runs over OOB rows only, or when the loss is
+    taken against the true targets.)"""
+    P, cols, live, sha, splits, cnts, pi, y = _stump_forest(1, 1)
+    N = cols.shape[1]
+    leafval = []
+    for (g, b), cnt in zip(splits, cnts):
+        left = cols[g] <= b
+        vals = {}
+        for side in (True, False):
+            m = left == side
+            vals[side] = Fraction(int((cnt[m].astype(object) * y[m].astype(object)).sum()), int(cnt[m].sum()))
+        leafval.append(vals)
+    imp = P.forest_permut(1, live, sha)
+    used = {g for g, _ in splits}
+    for f in range(cols.shape[0]):
+        if f not in used:
+            assert imp[f] == 0.0
+            continue
+        tot = Fraction(0)
+        for i in range(N):
+            d = (_forest_pred(cols, splits, leafval, i) - _forest_pred(cols, splits, leafval, i, f, pi[i]))
+            tot += (d * Fraction(1, 2**20)) ** 2
+        assert imp[f] == pytest.approx(float(tot / N), rel=1e-12)
+        assert imp[f] > 0
+
+
+@pytest.mark.parametrize("C", [2, 3])
+def test_forest_permut_classification_two_stumps_kl(C):
+    """Alg. 3 as printed, classification: the forest's predicted class
+    probabilities are the mean over trees of the leaves' class fractions;
+    imp[f] is the mean over all rows of KL(P~_base || P~_perm) with
+    P~_k = (P_k + eps) / (1 + C eps) -- recomputed from the raw labels in
+    exact rationals and 50-digit logarithms for a forest of two stumps."""
+    import decimal
+
+    P, cols, live, sha, splits, cnts, pi, y = _stump_forest(0, C)
+    N = cols.shape[1]
+    eps = Fraction(1e-7)
+    ctx = decimal.Context(prec=50)
+
+    def dec(q):
+        return ctx.divide(decimal.Decimal(q.numerator), decimal.Decimal(q.denominator))
+
+    leafvals = []  # per class: per tree: {side: fraction}
+    for k in range(C):
+        per_tree = []
+        for (g, b), cnt in zip(splits, cnts):
+            left = cols[g] <= b
+            per_tree.append({side: Fraction(int(cnt[(left == side) & (y == k)].sum()), int(cnt[left == side].sum()))
+                             for side in (True, False)})
+        leafvals.append(per_tree)
+    imp = P.forest_permut(1, live, sha)
+    used = {g for g, _ in splits}
+    for f in range(cols.shape[0]):
+        if f not in used:
+            assert imp[f] == 0.0
+            continue
+        tot = decimal.Decimal(0)
+        for i in range(N):
+            kl = decimal.Decimal(0)
+            for k in range(C):
+                a = (_forest_pred(cols, splits, leafvals[k], i) + eps) / (1 + C * eps)
+                c = (_forest_pred(cols, splits, leafvals[k], i, f, pi[i]) + eps) / (1 + C * eps)
+                if a != c:
+                    kl += ctx.multiply(dec(a), ctx.ln(dec(a / c)))
+            tot += kl
+        assert imp[f] == pytest.approx(float(tot / N), rel=1e-11)
+        assert imp[f] > 0
+
+
+def test_forest_permut_invariants_and_iteration():
+    """Alg. 3 as printed on a deeper forest: importances are >= 0, exactly 0
+    for columns no tree splits on and for a constant column; with
+    permut_form = 1 the iteration's hit statistic is that single row."""
+    w, _ = _small(importance=2, N=300, p=8, n_trees=6, max_depth=5)
+    X = w.X.copy()
+    X[2, :] = 3
+    P = oracle.BorutaProblem(X, w.y, **w.params(), N=w.N, permut_form=1)
+    live = np.arange(8, dtype=np.int32)
+    sha = P.shadow(1, live)
+    imp = P.forest_permut(1, live, sha)
+    used = set()
+    for tau in range(6):
+        nodes, _, _ = P.tree(1, live, sha, tau)
+        used |= {int(f) for f in nodes["feature"] if f >= 0}
+    assert (imp >= 0).all() and imp[2] == 0.0
+    for j in range(imp.size):
+        if j not in used:
+            assert imp[j] == 0.0
+    out = P.iteration(1, np.zeros(8, np.int8), np.zeros(8, np.int32))
+    np.testing.assert_array_equal(out["s"], imp)
+    np.testing.assert_array_equal(out["imp"], imp[None, :])
+    smax = imp[8:].max()
+    np.testing.assert_array_equal(out["hits"], (imp[:8] > smax).astype(np.int32))
+
+
 # ---------------------------------------------------------------- statistics
 
 def test_zscore_closed_forms():

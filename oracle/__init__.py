@@ -96,6 +96,8 @@ def lib():
             L.orc_tree.restype = ct.c_int
             L.orc_forest_permut.argtypes = [P(Problem), ct.c_int, vp, ct.c_int64, vp, vp]
             L.orc_forest_permut.restype = ct.c_int
+            L.orc_rank.argtypes = [ct.c_int64, ct.c_int32, vp, vp, vp]
+            L.orc_select_median.argtypes = [ct.c_int, ct.c_int64, ct.c_int32, vp, vp, vp, vp, P(ct.c_double), vp]
             L.orc_decide.argtypes = [ct.c_int, ct.c_double, ct.c_int64, vp, vp]
             L.orc_iteration.argtypes = [P(Problem), ct.c_int, vp, vp, vp, P(ct.c_double), vp, vp,
                                         P(ct.c_int64)]
@@ -186,6 +188,30 @@ def decide(t: int, alpha: float, hits, state):
     st = np.array(state, dtype=np.int8)
     lib().orc_decide(t, alpha, st.size, _ptr(hits), _ptr(st))
     return st
+
+
+def rank(decision, imp_history, iterations):
+    """Alg. 1's final ranking of a finished run (see oracle.h)."""
+    dec = np.ascontiguousarray(decision, dtype=np.int8)
+    hist = np.ascontiguousarray(imp_history, dtype=np.float64)
+    out = np.zeros(dec.size, np.int32)
+    lib().orc_rank(dec.size, iterations, _ptr(dec), _ptr(hist), _ptr(out))
+    return out
+
+
+def select_median(runs):
+    """Median selection over runs with different seeds (see oracle.h).
+    runs: list of run dicts (imp_history [max_iter, p], shadow_max,
+    iterations).  Returns (median importance [p], median shadow, selected)."""
+    hist = np.ascontiguousarray(np.stack([r["imp_history"] for r in runs]), dtype=np.float64)
+    smax = np.ascontiguousarray(np.stack([r["shadow_max"] for r in runs]), dtype=np.float64)
+    its = np.array([r["iterations"] for r in runs], dtype=np.int32)
+    n, T, p = hist.shape
+    med = np.zeros(p)
+    sel = np.zeros(p, np.int8)
+    ms = ct.c_double()
+    lib().orc_select_median(n, p, T, _ptr(its), _ptr(hist), _ptr(smax), _ptr(med), ct.byref(ms), _ptr(sel))
+    return med, ms.value, sel
 
 
 def node_split(task, n_classes, n_bins, bins, w, y, feats):

@@ -174,3 +174,72 @@ int orc_boruta(const orc_problem* P, int8_t* decision, int32_t* hits, double* im
   *iterations = t;
   return 0;
 }
+
+/* ---------------- after the loop ---------------- */
+
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+/* median of the non-NaN values among x[0], x[stride], ...; NaN if none
+ * (mean of the two middle values for an even count) */
+static double median_of(const double* x, int64_t n, int64_t stride, double* buf) {
+  int64_t m = 0;
+  for (int64_t k = 0; k < n; k++)
+    if (!isnan(x[k * stride])) buf[m++] = x[k * stride];
+  if (m == 0) return NAN;
+  qsort(buf, (size_t)m, sizeof(double), cmp_double);
+  return (m & 1) ? buf[m / 2] : (buf[m / 2 - 1] + buf[m / 2]) / 2.0;
+}
+
+void orc_rank(int64_t p, int32_t iterations, const int8_t* decision, const double* imp_history,
+              int32_t* rank) {
+  double* buf = (double*)malloc(sizeof(double) * (size_t)(iterations + 1));
+  double* med = (double*)malloc(sizeof(double) * (size_t)p);
+  int64_t* rej = (int64_t*)malloc(sizeof(int64_t) * (size_t)p);
+  int64_t nr = 0;
+  for (int64_t j = 0; j < p; j++) {
+    rank[j] = decision[j] == 1 ? 1 : 2;
+    if (decision[j] == -1) {
+      med[j] = median_of(imp_history + j, iterations, p, buf);
+      rej[nr++] = j;
+    }
+  }
+  /* rejected: 3, 4, ... by descending median (a NaN median last), ties to the lower index;
+   * a plain insertion sort of the rejected columns */
+  for (int64_t a = 1; a < nr; a++) {
+    int64_t j = rej[a], b = a;
+    while (b > 0) {
+      int64_t i = rej[b - 1];
+      int before = isnan(med[i]) ? 0 : (isnan(med[j]) ? 1 : (med[i] > med[j] || (med[i] == med[j] && i < j)));
+      if (before) break;
+      rej[b] = rej[b - 1];
+      b--;
+    }
+    rej[b] = j;
+  }
+  for (int64_t a = 0; a < nr; a++) rank[rej[a]] = (int32_t)(3 + a);
+  free(buf);
+  free(med);
+  free(rej);
+}
+
+void orc_select_median(int n_runs, int64_t p, int32_t max_iter, const int32_t* iterations,
+                       const double* imp_history, const double* shadow_max, double* med_imp,
+                       double* med_shadow, int8_t* selected) {
+  if (n_runs < 1 || max_iter < 1) return;
+  double* buf = (double*)malloc(sizeof(double) * (size_t)(max_iter + n_runs + 1));
+  double* per_run = (double*)malloc(sizeof(double) * (size_t)n_runs);
+  for (int64_t j = 0; j < p; j++) {
+    for (int r = 0; r < n_runs; r++)
+      per_run[r] = median_of(imp_history + (int64_t)r * max_iter * p + j, iterations[r], p, buf);
+    med_imp[j] = median_of(per_run, n_runs, 1, buf);
+  }
+  for (int r = 0; r < n_runs; r++)
+    per_run[r] = median_of(shadow_max + (int64_t)r * max_iter, iterations[r], 1, buf);
+  *med_shadow = median_of(per_run, n_runs, 1, buf);
+  for (int64_t j = 0; j < p; j++) selected[j] = med_imp[j] > *med_shadow;
+  free(buf);
+  free(per_run);
+}

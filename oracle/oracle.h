@@ -142,6 +142,25 @@ int orc_iteration(const orc_problem* P, int t, int8_t* state, int32_t* hits,
                   double* hist_row, double* shadow_max, double* imp, double* s,
                   int64_t* p_aug_out);
 
+/* ---- after the run ----
+ * orc_rank: Alg. 1's final ranking (its rankdata line is garbled; reading):
+ *   accepted 1, undecided 2, rejected 3, 4, ... by descending median of the
+ *   feature's history (iterations 1..iterations of imp_history, [max_iter][p],
+ *   NaN entries skipped), equal medians to the lower index.
+ * orc_select_median: the multi-seed selection of the paper's synthetic study
+ *   (20 runs, "the median importance as the basis for the final selection";
+ *   reading): per run r, m_rj = median of feature j's history and m_r = median
+ *   of the run's shadow maxima; med_imp[j] = median over runs of m_rj,
+ *   *med_shadow = median over runs of m_r; selected[j] = med_imp[j] >
+ *   *med_shadow.  imp_history is [n_runs][max_iter][p], shadow_max
+ *   [n_runs][max_iter]; medians of an even count take the mean of the two
+ *   middle values. */
+void orc_rank(int64_t p, int32_t iterations, const int8_t* decision, const double* imp_history,
+              int32_t* rank);
+void orc_select_median(int n_runs, int64_t p, int32_t max_iter, const int32_t* iterations,
+                       const double* imp_history, const double* shadow_max, double* med_imp,
+                       double* med_shadow, int8_t* selected);
+
 /* ---- the whole run ---- */
 int orc_boruta(const orc_problem* P, int8_t* decision, int32_t* hits,
                double* imp_history, double* shadow_max, int32_t* iterations);

@@ -799,6 +799,58 @@ def test_decision_step_random_runs():
     assert checked > 500
 
 
+# ---------------------------------------------------------------- after the run
+
+def test_final_ranking_hand_worked():
+    """Alg. 1's final ranking (reading of its garbled rankdata line):
+    accepted 1, tentative 2, rejected 3, 4, ... by descending median of the
+    feature's history over the iterations it was in play (NaN skipped, even
+    counts take the mean of the two middle values), equal medians to the
+    lower index.  Worked by hand: medians of the rejected columns 2, 3, 4, 6
+    are 0.5, 0.7, 0.5 and (0.1 + 0.3) / 2 = 0.2, so column 3 ranks 3, then
+    2 (lower index of the tie), 4, 6.  (Fails when the order is ascending,
+    the tie goes to the higher index, or the even median takes one value.)"""
+    nan = float("nan")
+    decision = np.array([1, 0, -1, -1, -1, 1, -1], np.int8)
+    hist = np.array([[0.9, 0.1, 0.5, 0.7, 0.6, 0.8, 0.1],
+                     [0.8, 0.2, 0.4, 0.9, 0.5, 0.9, 0.3],
+                     [0.9, 0.3, 0.6, 0.2, 0.4, 0.7, nan],
+                     [nan, nan, nan, nan, nan, nan, nan]])
+    got = oracle.rank(decision, hist, 3)
+    assert got.tolist() == [1, 2, 4, 3, 5, 1, 6]
+
+
+def test_median_selection_matches_numpy():
+    """Multi-seed selection (reading of the paper's 20-seed median rule):
+    per run the median of each feature's history and of the shadow maxima,
+    then the median over runs; a feature is selected when its median beats
+    the shadows' -- against numpy's nanmedian/median on random histories
+    with NaN gaps and runs of different lengths."""
+    rng = np.random.default_rng(5)
+    for n_runs in (1, 2, 5, 20):
+        T, p = 12, 9
+        runs = []
+        for r in range(n_runs):
+            it = int(rng.integers(1, T + 1))
+            h = np.full((T, p), np.nan)
+            h[:it] = rng.random((it, p))
+            h[:it][rng.random((it, p)) < 0.2] = np.nan
+            h[0] = rng.random(p)  # every feature in play at t = 1
+            sm = np.full(T, np.nan)
+            sm[:it] = rng.random(it)
+            runs.append(dict(imp_history=h, shadow_max=sm, iterations=it))
+        med, ms, sel = oracle.select_median(runs)
+        want = np.median(np.stack([np.nanmedian(r["imp_history"][:r["iterations"]], axis=0) for r in runs]), axis=0)
+        want_s = np.median([np.nanmedian(r["shadow_max"][:r["iterations"]]) for r in runs])
+        np.testing.assert_array_equal(med, want)
+        assert ms == want_s
+        np.testing.assert_array_equal(sel, (want > want_s).astype(np.int8))
+    # strict: a feature whose median equals the shadows' is not selected
+    h = np.array([[0.5, 0.6], [0.3, 0.6], [0.4, 0.6]])
+    med, ms, sel = oracle.select_median([dict(imp_history=h, shadow_max=np.array([0.2, 0.4, 0.9]), iterations=3)])
+    assert med.tolist() == [0.4, 0.6] and ms == 0.4 and sel.tolist() == [0, 1]
+
+
 # ---------------------------------------------------------------- end to end
 
 @pytest.mark.slow

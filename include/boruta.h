@@ -74,6 +74,14 @@ typedef struct {
   int chunk_nodes; /* band path: at most this many larger nodes per chunk (0 = as many as the
                       plan buffers hold, the default); results are identical whatever the value,
                       a small value runs the multi-chunk path on small problems */
+  int permut_form; /* Alg. 3 (task with BORUTA_PERMUT): 0 = each tree's out-of-bag rows against
+                      that tree's prediction, one importance row per tree (default); 1 = Alg. 3
+                      as printed: every row against the forest's prediction (mean over trees of
+                      the leaves' class fractions or means), one importance row for the forest,
+                      which is then the hit statistic (stat has no effect); its terms are FP64
+                      whatever `precision` says */
+  int forest_rows; /* permut_form = 1: rows per block of the (row, column) accumulators (0 = as
+                      many as fit in about 1 GiB, the default); results are identical */
 } boruta_opts;
 
 /* Host-side, caller-allocated outputs. */
@@ -193,7 +201,8 @@ int boruta_session_write(boruta_session* s, const int8_t* decision, const int32_
 /* Dumps of the last completed iteration, for parity checks.  what:
  *   BORUTA_DUMP_SHADOW   uint8  [n_sha * N]   shadow columns (Alg. 1 X_sha)
  *   BORUTA_DUMP_BOOT     uint32 [M * N]       bootstrap draw counts per tree
- *   BORUTA_DUMP_IMP      double [M * p_aug]   per-tree importance rows
+ *   BORUTA_DUMP_IMP      double [M * p_aug]   per-tree importance rows ([p_aug], one forest row,
+ *                                             with opts->permut_form = 1)
  *   BORUTA_DUMP_STAT     double [p_aug]       hit statistic per augmented column
  *   BORUTA_DUMP_NODES    boruta_node [count]  trees in order, each in (depth, heap) order
  *   BORUTA_DUMP_TREE_PTR int64  [M + 1]       offsets of each tree in the node dump
@@ -292,6 +301,43 @@ int boruta_binom_tails(const int32_t* t, const int32_t* h, double* p_acc, double
  * that overlap on the GPU race on it. */
 int boruta_binom_tails_noalloc(const int32_t* t, const int32_t* h, double* p_acc, double* p_rej,
                                int64_t n, void* stream);
+
+/* ---- after the run (host computations on host buffers; no GPU work) ----
+ *
+ * boruta_rank -- Alg. 1's final ranking of a finished run.  The algorithm's
+ *   rankdata line is garbled; the reading taken: accepted features rank 1,
+ *   tentative ones 2, rejected ones 3, 4, ... in descending order of the
+ *   median of their history (the rows 0..iterations-1 of imp_history,
+ *   [max_iter][p] as boruta_result holds it, NaN entries -- iterations out of
+ *   play -- skipped), equal medians to the lower column index.
+ *   decision [in] p values in {-1, 0, 1};  rank [out] int32[p].
+ *
+ * boruta_select_median -- the selection of the paper's synthetic study, which
+ *   ran 20 seeds and selected on the median importance (Sec. 3.1); the
+ *   reading taken: per run r, the median of each feature's history and the
+ *   median of the run's shadow maxima; median_imp[j] and *median_shadow are
+ *   the medians of those over the runs, and selected[j] = 1 when median_imp[j]
+ *   > *median_shadow (strict).  Medians skip NaN and take the mean of the two
+ *   middle values of an even count.
+ *   iterations [in] int32[n_runs]; imp_history [in] [n_runs][max_iter][p];
+ *   shadow_max [in] [n_runs][max_iter]; median_imp [out] double[p];
+ *   selected [out] int8[p].
+ *
+ * boruta_fit_seeds -- boruta_fit on one problem for each of n_seeds seeds,
+ *   run as independent jobs of one batch (boruta_fit_batch; job j uses
+ *   seeds[j] and the job id opts->job + j), then boruta_select_median over
+ *   the runs.  outs[j] receives run j (host buffers as boruta_fit's); X and y
+ *   as for boruta_fit (device pointers unless opts->host_inputs = 1).
+ *
+ * All three return BORUTA_EINVAL for bad sizes or NULL buffers. */
+int boruta_rank(const int8_t* decision, const double* imp_history, int64_t p, int32_t iterations, int32_t* rank);
+int boruta_select_median(int n_runs, int64_t p, int32_t max_iter, const int32_t* iterations,
+                         const double* imp_history, const double* shadow_max, double* median_imp,
+                         double* median_shadow, int8_t* selected);
+int boruta_fit_seeds(const uint8_t* X, int64_t ld, const void* y, int64_t N, int64_t p, int task, int n_trees,
+                     int max_depth, int mtry, int n_bins, int max_iter, double alpha, int n_seeds,
+                     const uint64_t* seeds, const boruta_opts* opts, boruta_result* outs, double* median_imp,
+                     double* median_shadow, int8_t* selected);
 
 /*
  * boruta_quantise -- float features to the uint8 bins the fit consumes (a

@@ -30,7 +30,7 @@ EXPORTS = [
     "boruta_session_kernel_stats", "boruta_session_importance_stats", "boruta_session_destroy",
     "boruta_philox", "boruta_perm",
     "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_quantise",
-    "boruta_last_error",
+    "boruta_last_error", "boruta_rank", "boruta_select_median", "boruta_fit_seeds",
 ]
 
 
@@ -44,7 +44,7 @@ class Opts(ct.Structure):
     _fields_ = [("stat", ct.c_int), ("precision", ct.c_int), ("tie_break", ct.c_int),
                 ("n_classes", ct.c_int), ("kl_eps", ct.c_double), ("stream", ct.c_void_p),
                 ("job", ct.c_uint32), ("host_inputs", ct.c_int), ("graph", ct.c_int), ("split_path", ct.c_int),
-                ("chunk_nodes", ct.c_int)]
+                ("chunk_nodes", ct.c_int), ("permut_form", ct.c_int), ("forest_rows", ct.c_int)]
 
 
 class Job(ct.Structure):
@@ -108,6 +108,10 @@ def lib():
         L.boruta_binom_tails_noalloc.argtypes = [vp, vp, vp, vp, i64, vp]
         L.boruta_quantise.argtypes = [vp, i64, i64, i64, ct.c_int, vp, i64, vp]
         L.boruta_last_error.restype = ct.c_char_p
+        L.boruta_rank.argtypes = [vp, vp, i64, ct.c_int32, vp]
+        L.boruta_select_median.argtypes = [i32, i64, ct.c_int32, vp, vp, vp, vp, ct.POINTER(ct.c_double), vp]
+        L.boruta_fit_seeds.argtypes = [vp, i64, vp, i64, i64, i32, i32, i32, i32, i32, i32, ct.c_double, i32, vp,
+                                       ct.POINTER(Opts), vp, vp, ct.POINTER(ct.c_double), vp]
         for name in EXPORTS:
             if name not in ("boruta_default_opts", "boruta_session_destroy", "boruta_batch_destroy",
                             "boruta_last_error"):
@@ -127,12 +131,12 @@ def _stream():
 
 
 def make_opts(stat=0, precision=0, tie_break=0, n_classes=0, kl_eps=1e-7, job=0, host_inputs=0,
-              graph=0, split_path=0, chunk_nodes=0, stream=None) -> Opts:
+              graph=0, split_path=0, chunk_nodes=0, permut_form=0, forest_rows=0, stream=None) -> Opts:
     o = Opts()
     lib().boruta_default_opts(ct.byref(o))
     o.stat, o.precision, o.tie_break, o.n_classes = stat, precision, tie_break, n_classes
     o.kl_eps, o.job, o.host_inputs, o.graph, o.split_path = kl_eps, job, host_inputs, graph, split_path
-    o.chunk_nodes = chunk_nodes
+    o.chunk_nodes, o.permut_form, o.forest_rows = chunk_nodes, permut_form, forest_rows
     o.stream = stream if stream is not None else (None if host_inputs else _stream())
     return o
 
@@ -371,3 +375,55 @@ def boruta_quantise(F, n_bins, N=None):
                                  _stream()))
     return out
 
+
+
+def boruta_rank(decision, imp_history, iterations):
+    """Alg. 1's final ranking of a finished run (host arrays)."""
+    dec = np.ascontiguousarray(decision, dtype=np.int8)
+    hist = np.ascontiguousarray(imp_history, dtype=np.float64)
+    out = np.zeros(dec.size, np.int32)
+    _check(lib().boruta_rank(dec.ctypes.data, hist.ctypes.data, dec.size, iterations, out.ctypes.data))
+    return out
+
+
+def boruta_select_median(runs):
+    """Median selection over runs with different seeds.  runs: list of run
+    dicts (imp_history [max_iter, p], shadow_max, iterations), as
+    boruta_fit returns them.  Returns (median importance, median shadow,
+    selected)."""
+    hist = np.ascontiguousarray(np.stack([r["imp_history"] for r in runs]), dtype=np.float64)
+    smax = np.ascontiguousarray(np.stack([r["shadow_max"] for r in runs]), dtype=np.float64)
+    its = np.array([r["iterations"] for r in runs], dtype=np.int32)
+    n, T, p = hist.shape
+    med = np.zeros(p)
+    sel = np.zeros(p, np.int8)
+    ms = ct.c_double()
+    _check(lib().boruta_select_median(n, p, T, its.ctypes.data, hist.ctypes.data, smax.ctypes.data, med.ctypes.data,
+                                      ct.byref(ms), sel.ctypes.data))
+    return med, ms.value, sel
+
+
+def boruta_fit_seeds(X, y, task, n_trees, max_depth, mtry, n_bins, max_iter, alpha, seeds, N=None, **opts):
+    """boruta_fit for each seed as jobs of one batch, then the median
+    selection.  Returns (runs, median importance, median shadow, selected)."""
+    host = opts.get("host_inputs", 0)
+    xp, ld, N, p, yp, keep = _xy(X, y, N, host)
+    o = make_opts(**opts)
+    sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+    res = (Result * len(sd))()
+    runs = []
+    for r in range(len(sd)):
+        run = dict(decision=np.zeros(p, np.int8), hits=np.zeros(p, np.int32),
+                   imp_history=np.zeros((max_iter, p)), shadow_max=np.zeros(max_iter))
+        res[r] = Result(run["decision"].ctypes.data, run["hits"].ctypes.data, run["imp_history"].ctypes.data,
+                        run["shadow_max"].ctypes.data, 0)
+        runs.append(run)
+    med = np.zeros(p)
+    sel = np.zeros(p, np.int8)
+    ms = ct.c_double()
+    _check(lib().boruta_fit_seeds(xp, ld, yp, N, p, task, n_trees, max_depth, mtry, n_bins, max_iter, alpha, len(sd),
+                                  sd.ctypes.data, ct.byref(o), res, med.ctypes.data, ct.byref(ms), sel.ctypes.data))
+    for r, run in enumerate(runs):
+        run["iterations"] = res[r].iterations
+    del keep
+    return runs, med, ms.value, sel

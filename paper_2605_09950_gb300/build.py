@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libboruta_gb300.so")
-SOURCES = ["api.cu", "kernels.cu", "split.cu", "noalloc.cu", "quantise.cu"]
+SOURCES = ["api.cu", "kernels.cu", "split.cu", "noalloc.cu", "quantise.cu", "rank.cu"]
 HEADERS = ["device.cuh", "engine.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no multiply-add contraction, so every floating-point operation

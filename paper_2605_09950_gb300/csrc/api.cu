@@ -51,6 +51,7 @@ int64_t isqrt(int64_t v) {
 
 // error reporting for noalloc.cu (same thread-local message as every entry point)
 int boruta_noalloc_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+int boruta_record_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 struct boruta_session {
   Dev d{};
@@ -149,6 +150,10 @@ static int check_args(const uint8_t* X, int64_t ld, const void* y, int64_t N, in
     return fail(BORUTA_EINVAL, "n_classes = %d outside [0, 8]", o->n_classes);
   if (o->split_path < 0 || o->split_path > 1) return fail(BORUTA_EINVAL, "opts: split_path takes 0 or 1");
   if (o->chunk_nodes < 0) return fail(BORUTA_EINVAL, "opts: chunk_nodes must not be negative");
+  if (o->permut_form < 0 || o->permut_form > 1) return fail(BORUTA_EINVAL, "opts: permut_form takes 0 or 1");
+  if (o->forest_rows < 0) return fail(BORUTA_EINVAL, "opts: forest_rows must not be negative");
+  if (o->permut_form == 1 && !(task & BORUTA_PERMUT))
+    return fail(BORUTA_EINVAL, "opts: permut_form = 1 is a form of Alg. 3 (task needs BORUTA_PERMUT)");
   if (o->precision < 0 || o->precision > 1 || o->tie_break < 0 || o->tie_break > 1 || o->stat < 0 ||
       o->stat > 1)
     return fail(BORUTA_EINVAL, "opts: precision, tie_break and stat take 0 or 1");
@@ -190,6 +195,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   d.M = n_trees;
   d.max_iter = max_iter;
   d.precision = o->precision;
+  d.permut_form = d.permut ? o->permut_form : 0;
   d.tie_break = o->tie_break;
   d.stat = o->stat;
   d.seed = seed;
@@ -351,6 +357,19 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
     if ((rc = s->alloc(&d.band_cnt, kMaxBands + 1))) return rc;
   }
   (void)Cmax;
+  if (d.permut_form == 1) {
+    // Alg. 3 as printed: per row the exact base sums; per block of rows the
+    // exact (row, column) deltas, blocks sized to about 1 GiB
+    const int64_t K = reg ? 1 : d.C;
+    const int64_t per_row = p_aug_max * K * kCsaLimbs * static_cast<int64_t>(sizeof(long long));
+    d.frows = static_cast<uint32_t>(std::max<int64_t>(1, std::min<int64_t>(N, (int64_t{1} << 30) / per_row)));
+    if (o->forest_rows > 0) d.frows = std::min<uint32_t>(d.frows, static_cast<uint32_t>(o->forest_rows));
+    if ((rc = s->alloc(&d.fbase, static_cast<size_t>(N) * K * kCsaLimbs))) return rc;
+    if ((rc = s->alloc(&d.fbase_mean, static_cast<size_t>(N) * K))) return rc;
+    if ((rc = s->alloc(&d.facc, static_cast<size_t>(d.frows) * p_aug_max * K * kCsaLimbs))) return rc;
+    CK(cudaMemsetAsync(d.facc, 0, static_cast<size_t>(d.frows) * p_aug_max * K * kCsaLimbs * sizeof(long long),
+                       s->st));
+  }
   CK(cudaMemsetAsync(d.status, 0, 4 * sizeof(uint32_t), s->st));
 
   // launch geometry
@@ -492,13 +511,22 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
     CK_LAUNCH("next-level kernels");
   }
   if (timed) CK(cudaEventRecord(s->iev[0], st));
-  if (d.permut)
+  if (d.permut_form == 1)
+    launch_forest_permut(d, s->permut_grid, st);
+  else if (d.permut)
     launch_permut(d, s->permut_grid, s->walk_grid, st);
   else
     launch_treeimp(d, s->tree_grid, st);
   CK_LAUNCH("importance kernels");
   if (timed) CK(cudaEventRecord(s->iev[1], st));
-  launch_stats_decide(d, st);
+  if (d.permut_form == 1) {  // one importance row for the forest: it is the hit statistic
+    Dev d1 = d;
+    d1.M = 1;
+    d1.stat = 1;
+    launch_stats_decide(d1, st);
+  } else {
+    launch_stats_decide(d, st);
+  }
   CK_LAUNCH("k_stats / k_decide");
   CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->state_pin, d.state, s->p, cudaMemcpyDeviceToHost, st));
@@ -699,7 +727,8 @@ int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacit
     case BORUTA_DUMP_BOOT:
       return copy_out(s, d.bootcnt, static_cast<int64_t>(d.M) * d.N * 4, host, capacity, bytes);
     case BORUTA_DUMP_IMP:
-      return copy_out(s, d.imp, static_cast<int64_t>(d.M) * d.p_aug * 8, host, capacity, bytes);
+      return copy_out(s, d.imp, static_cast<int64_t>(d.permut_form == 1 ? 1 : d.M) * d.p_aug * 8, host, capacity,
+                      bytes);
     case BORUTA_DUMP_STAT:
       return copy_out(s, d.s, static_cast<int64_t>(d.p_aug) * 8, host, capacity, bytes);
     case BORUTA_DUMP_LIVE:

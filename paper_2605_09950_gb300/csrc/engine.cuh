@@ -18,6 +18,7 @@ struct Dev {
   const int64_t* yreg;     // fixed-point targets (regression)
   int32_t N, ldN, p, kind, C, B, D, M, max_iter;
   int32_t precision, tie_break, stat, permut;
+  int32_t permut_form;           // Alg. 3 rows: 0 = each tree's OOB rows, 1 = all rows, forest prediction
   uint64_t seed;
   uint32_t job;
   double kl_eps, alpha;
@@ -67,6 +68,11 @@ struct Dev {
   double* hist;                  // [max_iter][p]
   double* smax;                  // [max_iter]
   uint32_t* status;              // [0] error flags, [1] undecided count, [2] n_classes seen
+  // ---- Alg. 3 as printed (permut_form = 1)
+  long long* fbase;              // [N][K][kCsaLimbs] exact sum over trees of each row's leaf value
+  double* fbase_mean;            // [N][K] the forest's prediction (K = C, or 1 for regression)
+  long long* facc;               // [frows][p_aug][K][kCsaLimbs] per (row of the block, column) delta
+  uint32_t frows;                // rows per block
   unsigned long long* counters;  // [0] split-stage algorithmic bytes, [1] max |y|,
                                  // [2] histogram-kernel algorithmic bytes,
                                  // [3] node visits of the Alg. 3 tree walks
@@ -110,6 +116,7 @@ void launch_gather_live(const Dev& d, cudaStream_t st);
 void launch_children(const Dev& d, int level, cudaStream_t st);
 void launch_treeimp(const Dev& d, int grid, cudaStream_t st);
 void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st);
+void launch_forest_permut(const Dev& d, int grid, cudaStream_t st);
 const void* permut_kernel_ptr();  // for its occupancy
 void launch_stats_decide(const Dev& d, cudaStream_t st);
 // Warp-private histogram layout.  A lane scans 8 consecutive bins, so one

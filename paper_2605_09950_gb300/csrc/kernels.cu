@@ -642,6 +642,166 @@ void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
 
 const void* permut_kernel_ptr() { return reinterpret_cast<const void*>(&k_permut); }
 
+// ============================================================ Alg. 3 as printed: all rows, forest
+// The model is the whole forest: a row's prediction is the mean over the M
+// trees of its leaf's value (class fractions c_k/n, or the leaf mean S/n in
+// units of 2^-20).  Per row, the exact sum of the per-tree values (carry-save
+// fixed point) is kept in fbase; for a block of rows, facc holds per (row,
+// column f) the exact sum over the trees whose leaf changes when the row's
+// value of f is read at flush_index of (value of the new leaf - value of the
+// old leaf), so base + delta is exactly the sum over every tree of the
+// permuted prediction.  Each mean is that exact sum rounded once, then
+// divided by M (IEEE), and the per-row losses are summed exactly per column.
+
+__device__ __forceinline__ double leaf_value(const Dev& d, uint32_t q, int k) {
+  const double n = static_cast<double>(d.nd_n[q]);
+  return d.kind != 0 ? static_cast<double>(d.nd_S[q]) / n
+                     : static_cast<double>(d.nd_cnt[static_cast<int64_t>(q) * d.C + k]) / n;
+}
+
+// leaf of tree tau for row i (column f, if >= 0, read at row pi instead)
+__device__ __forceinline__ uint32_t forest_walk(const Dev& d, int tau, uint32_t i, uint32_t f, uint32_t pi) {
+  uint32_t k = static_cast<uint32_t>(tau);
+  for (int guard = 0; guard <= kMaxDepth; ++guard) {  // trees are at most kMaxDepth deep
+    const uint32_t s = d.nd_split[k];
+    if (s == kLeaf) break;
+    const uint32_t g = s >> 8;
+    const uint8_t x = d.Xaug[static_cast<int64_t>(g) * d.ldN + (g == f ? pi : i)];
+    k = d.nd_child[k] + (x > (s & 255u) ? 1u : 0u);
+  }
+  return k;
+}
+
+__host__ __device__ __forceinline__ int forest_k(const Dev& d) { return d.kind != 0 ? 1 : d.C; }
+
+// one thread per (tree, row): the row's leaf value into its exact base sum
+__global__ void k_fperm_base(Dev d) {
+  const int K = forest_k(d);
+  const int64_t items = static_cast<int64_t>(d.M) * d.N;
+  for (int64_t it = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; it < items;
+       it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int tau = static_cast<int>(it / d.N);
+    const uint32_t i = static_cast<uint32_t>(it - static_cast<int64_t>(tau) * d.N);
+    const uint32_t q = forest_walk(d, tau, i, 0xFFFFFFFFu, 0u);
+    for (int k = 0; k < K; ++k)
+      if (!csa_add(d.fbase + (static_cast<int64_t>(i) * K + k) * kCsaLimbs, leaf_value(d, q, k)))
+        atomicOr(&d.status[0], kErrAcc);
+  }
+}
+
+// the forest's own prediction per row (the exact sums rounded once, / M)
+__global__ void k_fperm_base_mean(Dev d) {
+  const int K = forest_k(d);
+  const int64_t items = static_cast<int64_t>(d.N) * K;
+  for (int64_t it = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; it < items;
+       it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    uint64_t a[kFixLimbs];
+    csa_to_fix(d.fbase + it * kCsaLimbs, a);
+    d.fbase_mean[it] = fix_to_double(a) / static_cast<double>(d.M);
+  }
+}
+
+// One thread per (tree, row of the block): the row's path; for each distinct
+// column f on it, the leaf reached with f read at flush_index (the walk
+// leaves the path at the first node testing f that sends the swapped value
+// the other way); a changed leaf adds (new - old) per class to (row, f).
+__global__ void k_fperm_delta(Dev d, uint32_t r0, uint32_t rows) {
+  const int K = forest_k(d);
+  const int64_t items = static_cast<int64_t>(d.M) * rows;
+  for (int64_t it = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; it < items;
+       it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int tau = static_cast<int>(it / rows);
+    const uint32_t loc = static_cast<uint32_t>(it - static_cast<int64_t>(tau) * rows);
+    const uint32_t i = r0 + loc;
+    const uint32_t pi = d.piv[i];
+    uint32_t pw[kMaxDepth];
+    int depth = 0;
+    uint32_t k = static_cast<uint32_t>(tau);
+    for (uint32_t s = d.nd_split[k]; s != kLeaf && depth < kMaxDepth; s = d.nd_split[k]) {
+      const uint8_t x = d.Xaug[static_cast<int64_t>(s >> 8) * d.ldN + i];
+      pw[depth++] = s;
+      k = d.nd_child[k] + (x > (s & 255u) ? 1u : 0u);
+    }
+    const uint32_t q = k;
+    for (int a = 0; a < depth; ++a) {  // a column off the path leaves the leaf unchanged
+      const uint32_t f = pw[a] >> 8;
+      bool seen = false;
+      for (int b = 0; b < a; ++b) seen |= (pw[b] >> 8) == f;
+      if (seen) continue;
+      const uint32_t q2 = forest_walk(d, tau, i, f, pi);
+      if (q2 == q) continue;
+      long long* acc = d.facc + ((static_cast<int64_t>(loc) * d.p_aug + f) * K) * kCsaLimbs;
+      bool ok = true;
+      for (int c = 0; c < K; ++c) {
+        ok &= csa_add(acc + c * kCsaLimbs, leaf_value(d, q2, c));
+        ok &= csa_add(acc + c * kCsaLimbs, -leaf_value(d, q, c));
+      }
+      if (!ok) atomicOr(&d.status[0], kErrAcc);
+    }
+  }
+}
+
+// One thread per (row of the block, column): the loss between the forest's
+// prediction and its prediction with the column permuted, summed exactly
+// per column; the thread clears the (row, column) accumulators it read.
+__global__ void k_fperm_loss(Dev d, uint32_t r0, uint32_t rows) {
+  const int K = forest_k(d);
+  const int64_t items = static_cast<int64_t>(rows) * d.p_aug;
+  for (int64_t it = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; it < items;
+       it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t loc = static_cast<uint32_t>(it / d.p_aug);
+    const uint32_t f = static_cast<uint32_t>(it - static_cast<int64_t>(loc) * d.p_aug);
+    const uint32_t i = r0 + loc;
+    long long* acc = d.facc + ((static_cast<int64_t>(loc) * d.p_aug + f) * K) * kCsaLimbs;
+    double L = 0.0;
+    const double eps = d.kl_eps, norm = 1.0 + static_cast<double>(d.C) * eps;
+    for (int c = 0; c < K; ++c) {
+      bool zero = true;
+#pragma unroll
+      for (int l = 0; l < kCsaLimbs; ++l) zero &= acc[c * kCsaLimbs + l] == 0;
+      if (zero) continue;  // no tree's leaf changed for this class value
+      uint64_t a[kFixLimbs], b[kFixLimbs];
+      csa_to_fix(d.fbase + (static_cast<int64_t>(i) * K + c) * kCsaLimbs, a);
+      csa_to_fix(acc + c * kCsaLimbs, b);
+      fix_add(a, b);
+      const double perm = fix_to_double(a) / static_cast<double>(d.M);
+      const double base = d.fbase_mean[static_cast<int64_t>(i) * K + c];
+#pragma unroll
+      for (int l = 0; l < kCsaLimbs; ++l) acc[c * kCsaLimbs + l] = 0;
+      if (d.kind != 0) {
+        const double df = (base - perm) * 0x1p-20;
+        L += df * df;
+      } else {
+        const double pa = (base + eps) / norm, pb = (perm + eps) / norm;
+        L += pa * log(pa / pb);
+      }
+    }
+    if (L != 0.0 && !csa_add(d.acc + static_cast<int64_t>(f) * kCsaLimbs, L)) atomicOr(&d.status[0], kErrAcc);
+  }
+}
+
+// imp[f] = (exact sum over rows of the losses, rounded once) / N
+__global__ void k_fperm_final(Dev d) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d.p_aug; f += gridDim.x * blockDim.x) {
+    uint64_t a[kFixLimbs];
+    csa_to_fix(d.acc + static_cast<int64_t>(f) * kCsaLimbs, a);
+    d.imp[f] = fix_to_double(a) / static_cast<double>(d.N);
+  }
+}
+
+void launch_forest_permut(const Dev& d, int grid, cudaStream_t st) {
+  k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
+  cudaMemsetAsync(d.fbase, 0, static_cast<size_t>(d.N) * forest_k(d) * kCsaLimbs * sizeof(long long), st);
+  k_fperm_base<<<grid, 256, 0, st>>>(d);
+  k_fperm_base_mean<<<grid, 256, 0, st>>>(d);
+  for (uint32_t r0 = 0; r0 < static_cast<uint32_t>(d.N); r0 += d.frows) {
+    const uint32_t rows = min(d.frows, static_cast<uint32_t>(d.N) - r0);
+    k_fperm_delta<<<grid, 256, 0, st>>>(d, r0, rows);
+    k_fperm_loss<<<grid, 256, 0, st>>>(d, r0, rows);
+  }
+  k_fperm_final<<<(d.p_aug + 255) / 256, 256, 0, st>>>(d);
+}
+
 // ============================================================ Alg. 1: statistic, hits, test
 // s_j over trees, exact sums rounded once:
 //   mean = RN(sum imp)/M,  sd = sqrt(RN(sum (imp - mean)^2)/(M-1)),  Z = mean/(sd/sqrt(M))

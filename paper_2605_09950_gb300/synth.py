@@ -166,6 +166,53 @@ def multiclass_toeplitz(N=1_000_000, p=500, block=10, n_inf=25, n_classes=5, see
                     n_trees, max_depth, max_iter, seed=seed, informative=inf)
 
 
+# the paper's synthetic regression study (Sec. 3.1): 1-based column names of
+# the ten variables its target uses, and the five collinear columns of the
+# multicollinearity variant with the four variables each one combines
+PAPER_INFORMATIVE = (14, 18, 20, 26, 27, 31, 33, 40, 46, 49)
+PAPER_COLLINEAR = {13: ((14, 0.1), (40, 0.2), (7, 0.3), (42, 0.4)),
+                   5: ((31, 0.4), (46, 0.2), (47, 0.3), (48, 0.1)),
+                   38: ((18, 0.1), (49, 0.3), (16, 0.2), (10, 0.4)),
+                   9: ((27, 0.4), (26, 0.3), (17, 0.2), (25, 0.1)),
+                   4: ((33, 0.2), (20, 0.4), (35, 0.1), (32, 0.3))}
+
+
+def paper_regression(variant="direct", N=10_000, seed=0, n_trees=100, max_depth=16, max_iter=100, n_bins=128,
+                     importance=PERMUT, mtry=1 << 20) -> Workload:
+    """The paper's synthetic regression data (Sec. 3.1): X_1..X_50 ~ U(0, 1)
+    and y = 5 X27^3 + 4 X49^2 + 5 X31 X46 + 2 X14 - 2.5 X40 + 3.5 X18^(1/3)
+    + exp(X20) + 2 sin(3.14 X26) + 5 cos(3.14 X33) + eps1, eps1 ~ N(0, 1e-5)
+    (read as the variance); 10,000 rows; the other 40 columns are noise.
+    variant "biased" (Sec. 3.1.2): 99% of the rows, drawn at random, have
+    X20 = -1.0 before the target is formed; "collinear" (Sec. 3.1.3): X13,
+    X5, X38, X9 and X4 are replaced by the paper's linear combinations of
+    four other columns plus eps2 ~ N(0, 0.01) (variance).  Targets are int64
+    fixed point at 2^-20; features are quantile bins.  The forest defaults
+    are those of the regression forest the paper used (cuML's
+    RandomForestRegressor: 100 trees, depth 16, 128 bins, every column tried
+    at each split -- mtry clamps to the augmented width).  `informative`
+    holds the 0-based columns of the ten target variables."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    p = 50
+    F = rng.uniform(0.0, 1.0, size=(p, N))
+    x = lambda i: F[i - 1]  # 1-based names of the paper
+    if variant == "biased":
+        rows = rng.choice(N, size=int(round(0.99 * N)), replace=False)
+        F[19, rows] = -1.0
+    elif variant == "collinear":
+        for dst, terms in PAPER_COLLINEAR.items():
+            F[dst - 1] = sum(w * x(src) for src, w in terms) + rng.normal(0.0, math.sqrt(0.01), size=N)
+    elif variant != "direct":
+        raise ValueError(f"unknown variant {variant!r}")
+    yv = (5 * x(27) ** 3 + 4 * x(49) ** 2 + 5 * x(31) * x(46) + 2 * x(14) - 2.5 * x(40) + 3.5 * np.cbrt(x(18))
+          + np.exp(x(20)) + 2 * np.sin(3.14 * x(26)) + 5 * np.cos(3.14 * x(33)))
+    yv = yv + rng.normal(0.0, math.sqrt(1e-5), size=N)
+    y_fx = np.rint(yv * 2.0**20).astype(np.int64)
+    inf = np.array([i - 1 for i in PAPER_INFORMATIVE])
+    return Workload(f"paper_{variant}_N{N}", quantise(F, n_bins), y_fx, N, p, REGRESSION | importance, 1, n_bins,
+                    n_trees, max_depth, max_iter, seed=seed, mtry=mtry, informative=inf)
+
+
 def batch_jobs(n_jobs=64, seed=4, n_trees=200, max_depth=10, max_iter=50, n_bins=128,
                N_range=(500, 50_000), p_range=(20, 5000), quantiser=None) -> list[Workload]:
     """Independent classification problems of uneven size: N and p

@@ -114,3 +114,30 @@ def test_quantise_and_batch_reject_bad_arguments_on_the_host(lib):
     assert L.boruta_batch_run(None, 1, ct.byref(running)) == -1
     assert L.boruta_batch_read(None, 0, None, None, None, None, None) == -1
     L.boruta_batch_destroy(None)
+
+
+def test_rank_and_median_selection_match_the_oracle(lib):
+    """The library's host-side ranking and median selection (no GPU) equal
+    the oracle's on random finished runs with NaN gaps and ties."""
+    import oracle
+    from paper_2605_09950_gb300 import boruta
+
+    rng = np.random.default_rng(11)
+    for trial in range(30):
+        T, p = int(rng.integers(1, 15)), int(rng.integers(1, 30))
+        runs = []
+        for r in range(int(rng.integers(1, 8))):
+            it = int(rng.integers(1, T + 1))
+            h = np.full((T, p), np.nan)
+            h[:it] = np.round(rng.random((it, p)) * 4) / 4  # coarse values: ties
+            h[1:it][rng.random((it - 1, p)) < 0.3] = np.nan
+            sm = np.full(T, np.nan)
+            sm[:it] = np.round(rng.random(it) * 4) / 4
+            dec = rng.integers(-1, 2, size=p).astype(np.int8)
+            runs.append(dict(imp_history=h, shadow_max=sm, iterations=it, decision=dec))
+            np.testing.assert_array_equal(boruta.boruta_rank(dec, h, it), oracle.rank(dec, h, it))
+        got = boruta.boruta_select_median(runs)
+        want = oracle.select_median(runs)
+        np.testing.assert_array_equal(got[0], want[0])
+        assert got[1] == want[1]
+        np.testing.assert_array_equal(got[2], want[2])

@@ -88,3 +88,38 @@ def test_stepwise_batch_matches_fit_batch():
         for key in ("decision", "hits", "imp_history", "shadow_max"):
             np.testing.assert_array_equal(got[key], want[j][key], err_msg=f"job {j} {key}")
     R.close()
+
+
+def test_fit_seeds_matches_oracle_runs_and_median_selection():
+    """boruta_fit_seeds: the seeds run as jobs of one batch; every run equals
+    the oracle's run with that seed (and job id), and the median selection
+    and the final ranking of each run equal the oracle's."""
+    import torch
+
+    import __graft_entry__
+    from paper_2605_09950_gb300 import boruta
+
+    __graft_entry__.build()
+    w = synth.paper_regression("direct", N=600, n_trees=12, max_depth=6, max_iter=8, importance=synth.TREEIMP,
+                               mtry=0)
+    seeds = [3, 17, 29, 41, 57]
+    params = w.params()
+    params.pop("seed")
+    nc = params.pop("n_classes")
+    runs, med, ms, sel = boruta.boruta_fit_seeds(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.y).cuda(),
+                                                 seeds=seeds, N=w.N, n_classes=nc, job=2, **params)
+    want = []
+    for j, sd in enumerate(seeds):
+        o = oracle.BorutaProblem(w.X, w.y, **{**w.params(), "seed": sd}, N=w.N, job=2 + j).run()
+        g = runs[j]
+        assert g["iterations"] == o["iterations"]
+        for key in ("decision", "hits", "imp_history", "shadow_max"):
+            np.testing.assert_array_equal(g[key], o[key], err_msg=f"seed {sd} {key}")
+        np.testing.assert_array_equal(boruta.boruta_rank(g["decision"], g["imp_history"], g["iterations"]),
+                                      oracle.rank(o["decision"], o["imp_history"], o["iterations"]))
+        want.append(o)
+    om, oms, osel = oracle.select_median(want)
+    np.testing.assert_array_equal(med, om)
+    assert ms == oms
+    np.testing.assert_array_equal(sel, osel)
+    assert sel[w.informative].sum() >= 5  # the strong target variables stand out already at this size

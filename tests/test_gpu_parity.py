@@ -370,6 +370,71 @@ def test_band_path_in_many_chunks(case):
     assert levels[:, 0].max() > 3 * 3  # some level held more than three chunks of nodes
 
 
+# ---------------------------------------------------------------- Alg. 3 as printed
+
+@pytest.mark.parametrize("case,rows", [("binary", 0), ("binary", 37), ("multiclass", 0), ("multiclass", 100),
+                                       ("regression", 0), ("regression", 64)])
+def test_forest_permut_form_iteration(case, rows):
+    """opts.permut_form = 1 (every row against the forest's prediction, one
+    importance row for the forest, which is the hit statistic), with the
+    default row blocks and with several blocks (forest_rows): trees node by
+    node, the importance row (regression bit-exact, KL within 1e-12), the
+    statistic, hits and decisions against the oracle."""
+    from paper_2605_09950_gb300 import boruta
+
+    if case == "binary":
+        w = synth.binary_small(N=500, p=12, n_inf=3, n_trees=12, max_depth=7, max_iter=5, importance=2)
+    elif case == "multiclass":
+        w = synth.multiclass_toeplitz(N=1500, p=16, block=4, n_inf=3, n_classes=4, n_trees=8, max_depth=8,
+                                      max_iter=3, importance=2)
+    else:
+        w = synth.snp_regression(N=700, p=20, n_add=4, n_pairs=2, n_trees=8, max_depth=7, max_iter=3,
+                                 importance=2)
+    S = session(w, permut_form=1, forest_rows=rows)
+    S.step()
+    P = oracle_problem(w, permut_form=1)
+    live = np.arange(w.p, dtype=np.int32)
+    sha = P.shadow(1, live)
+    nodes = S.dump(boruta.DUMP_NODES, boruta.NODE_DTYPE)
+    ptr = S.dump(boruta.DUMP_TREE_PTR, np.int64)
+    for tau in range(w.n_trees):
+        nd, _, _ = P.tree(1, live, sha, tau)
+        compare_nodes(nodes[ptr[tau]:ptr[tau + 1]], nd)
+    imp = S.dump(boruta.DUMP_IMP, np.float64)
+    want = P.forest_permut(1, live, sha)
+    if case == "regression":
+        np.testing.assert_array_equal(imp, want)
+    else:
+        close(imp, want, REL64)
+    assert (imp > 0).any()
+    np.testing.assert_array_equal(S.dump(boruta.DUMP_STAT, np.float64), imp)
+    o = P.iteration(1, np.zeros(w.p, np.int8), np.zeros(w.p, np.int32))
+    g = S.read()
+    np.testing.assert_array_equal(g["hits"], o["hits"])
+    np.testing.assert_array_equal(g["decision"], o["state"])
+
+
+def test_forest_permut_form_full_run():
+    """A whole Boruta run with Alg. 3 as printed, through boruta_fit:
+    iterations, decisions and hits equal the oracle's run; the history of
+    the statistic within 1e-12."""
+    import torch
+
+    from paper_2605_09950_gb300 import boruta
+
+    w = synth.binary_small(N=400, p=10, n_inf=3, n_trees=16, max_depth=6, max_iter=18, importance=2)
+    params = w.params()
+    nc = params.pop("n_classes")
+    g = boruta.boruta_fit(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.y).cuda(), N=w.N, n_classes=nc,
+                          permut_form=1, **params)
+    o = oracle_problem(w, permut_form=1).run()
+    assert g["iterations"] == o["iterations"]
+    np.testing.assert_array_equal(g["decision"], o["decision"])
+    np.testing.assert_array_equal(g["hits"], o["hits"])
+    close(g["imp_history"], o["imp_history"], REL64)
+    assert (g["decision"] != 0).any()
+
+
 # ---------------------------------------------------------------- full-size workloads, sampled
 
 def _importance_properties(S, nodes, ptr, n_trees, permut):

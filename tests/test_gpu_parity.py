@@ -226,9 +226,14 @@ def test_full_run_small(importance):
         close(g["shadow_max"], o["shadow_max"], 1e-9)
 
 
-def test_binary_n1000_p50_full_run():
+@pytest.mark.parametrize("tie_break", [0, 1])
+def test_binary_n1000_p50_full_run(tie_break):
     """The small workload: binary N=1000, p=50, 100 trees, depth 8, TreeImp,
-    20 iterations -- bit-exact against the oracle, planted set recovered."""
+    20 iterations -- bit-exact against the oracle under either tie rule; the
+    planted set is accepted (exactly it when ties go to the feature drawn
+    first; with ties to the lowest index real columns also win the ties of
+    tiny nodes against the higher-indexed shadows, so noise columns can be
+    accepted too)."""
     import torch
 
     from paper_2605_09950_gb300 import boruta
@@ -237,13 +242,16 @@ def test_binary_n1000_p50_full_run():
     params = w.params()
     nc = params.pop("n_classes")
     g = boruta.boruta_fit(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.y).cuda(), N=w.N, n_classes=nc,
-                          **params)
-    o = oracle_problem(w).run()
+                          tie_break=tie_break, **params)
+    o = oracle_problem(w, tie_break=tie_break).run()
     assert g["iterations"] == o["iterations"]
     np.testing.assert_array_equal(g["decision"], o["decision"])
     np.testing.assert_array_equal(g["hits"], o["hits"])
     np.testing.assert_array_equal(g["imp_history"], o["imp_history"])
-    assert set(np.flatnonzero(g["decision"] == 1)) == set(w.informative.tolist())
+    accepted = set(np.flatnonzero(g["decision"] == 1))
+    assert set(w.informative.tolist()) <= accepted
+    if tie_break == 1:
+        assert accepted == set(w.informative.tolist())
 
 
 @pytest.mark.parametrize("importance", [synth.TREEIMP, synth.PERMUT])

@@ -45,7 +45,8 @@ typedef enum {
   BORUTA_OK = 0,
   BORUTA_EINVAL = -1,    /* bad argument, size or input value */
   BORUTA_EOVERFLOW = -2, /* an integer bound guard tripped (weights, sums, pools) */
-  BORUTA_ETIMEOUT = -3,  /* a bounded device wait gave up */
+  BORUTA_ETIMEOUT = -3,  /* reserved: no kernel of this library waits on another (no device
+                            barrier, no spin), so no call returns it */
   BORUTA_ECUDA = -4,     /* a CUDA runtime call failed */
   BORUTA_ENOMEM = -5     /* device workspace allocation failed */
 } boruta_status;

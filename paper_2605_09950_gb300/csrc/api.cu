@@ -241,6 +241,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   if ((rc = s->alloc(&d.oob, MN))) return rc;
   if ((rc = s->alloc(&d.oob_cnt, n_trees))) return rc;
   if (d.permut && (rc = s->alloc(&d.piv, static_cast<size_t>(N)))) return rc;
+  if (d.permut && (rc = s->alloc(&d.Xrow, static_cast<size_t>(N) * ((p_aug_max + 15) / 16 * 16)))) return rc;
   const size_t P = cap;
   if ((rc = s->alloc(&d.nd_tree, P))) return rc;
   if ((rc = s->alloc(&d.nd_heap, P))) return rc;
@@ -249,6 +250,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   if ((rc = s->alloc(&d.nd_n, P))) return rc;
   if ((rc = s->alloc(&d.nd_split, P))) return rc;
   if ((rc = s->alloc(&d.nd_child, P))) return rc;
+  if (d.permut && (rc = s->alloc(&d.nd_sc, P))) return rc;
   if ((rc = s->alloc(&d.nd_delta, P))) return rc;
   if ((rc = s->alloc(&d.nd_lrows, P))) return rc;
   if ((rc = s->alloc(&d.nd_ln, P))) return rc;
@@ -458,6 +460,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   int64_t m = s->mtry_opt > 0 ? std::min<int64_t>(s->mtry_opt, p_aug)
                               : (d.kind ? p_aug / 3 : isqrt(p_aug));
   d.mtry = static_cast<int32_t>(std::max<int64_t>(m, 1));
+  d.ldP = static_cast<int32_t>((p_aug + 15) / 16 * 16);
   // feature bands: ~kBandBytes of columns each, at most kMaxBands; the packed
   // item holds a 14-bit slot and a 22-bit feature
   d.band_w = 0;
@@ -602,7 +605,6 @@ static int step_finish(boruta_session* s, int32_t* undecided) {
     if (err & kErrPool) return fail(BORUTA_EOVERFLOW, "node pool capacity (%u) exceeded", d.cap);
     if (err & kErrWeight) return fail(BORUTA_EOVERFLOW, "a bootstrap count exceeded 255");
     if (err & kErrAcc) return fail(BORUTA_EOVERFLOW, "an importance term left the exact accumulator range");
-    if (err & kErrTimeout) return fail(BORUTA_ETIMEOUT, "a bounded device wait gave up");
     return fail(BORUTA_EINVAL, "device reported error flags 0x%x", err);
   }
   s->split_ms = 0.0;

@@ -27,7 +27,6 @@ enum : uint32_t {
   kErrPool = 1u,      // node pool capacity exceeded
   kErrWeight = 2u,    // a bootstrap count exceeded 255
   kErrAcc = 4u,       // an accumulator term outside the fixed-point window
-  kErrTimeout = 8u,   // a bounded wait gave up
   kErrInput = 16u,    // a bin >= n_bins or a label >= n_classes
 };
 

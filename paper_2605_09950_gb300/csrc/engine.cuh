@@ -32,12 +32,17 @@ struct Dev {
   uint32_t* oob;                 // [M][N] out-of-bag rows, ascending
   uint32_t* oob_cnt;             // [M]
   uint32_t* piv;                 // [N] Alg. 3 flush_index of the iteration (Permut only)
+  uint8_t* Xrow;                 // [N][ldP] row-major copy of Xaug for the Alg. 3 walks (Permut only):
+                                 //   a walk reads one row's bins again and again, and a row's
+                                 //   record stays in cache where its columns would not
+  int32_t ldP;                   // round16(p_aug) of the iteration
   // ---- node pool (level-major; within a level, ordered by (tree, heap))
   uint32_t cap;
   uint32_t *nd_tree, *nd_heap, *nd_seg, *nd_len, *nd_n;
   uint32_t* nd_cnt;              // [cap][C] weighted class counts
   int64_t* nd_S;                 // [cap] weighted target sum
   uint32_t *nd_split, *nd_child; // split = feature << 8 | bin, kLeaf for leaves
+  uint2* nd_sc;                  // (split, child) of every node, packed for the Alg. 3 walks (Permut only)
   double* nd_delta;
   uint32_t *nd_lrows, *nd_ln;    // left child: distinct rows, weighted rows
   uint32_t* nd_lcnt;             // [cap][C]

@@ -419,6 +419,35 @@ void launch_treeimp(const Dev& d, int grid, cudaStream_t st) {
 }
 
 // ============================================================ Alg. 3 on OOB rows
+// (split, child) of every node of the iteration's trees in one array, so that
+// a walk step loads both children's words with two 8-byte loads.
+__global__ void k_pack_nodes(Dev d) {
+  const uint32_t total = d.lvl_off[d.D] + d.lvl_cnt[d.D];
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x)
+    d.nd_sc[k] = make_uint2(d.nd_split[k], d.nd_child[k]);
+}
+
+// Row-major copy of the augmented matrix for the tree walks: Xrow[i][f] =
+// Xaug[f][i].  One 64 x 64 tile per block through shared memory: the reads
+// run along the rows of a column, the writes along the columns of a row.
+__global__ void __launch_bounds__(256) k_transpose_rows(Dev d) {
+  __shared__ uint8_t tile[64][65];
+  const int tiles_i = (d.N + 63) / 64, tiles_f = (d.p_aug + 63) / 64;
+  for (int t = blockIdx.x; t < tiles_i * tiles_f; t += gridDim.x) {
+    const int i0 = (t % tiles_i) * 64, f0 = (t / tiles_i) * 64;
+    for (int k = threadIdx.x; k < 64 * 64; k += blockDim.x) {
+      const int f = k >> 6, i = k & 63;
+      if (f0 + f < d.p_aug && i0 + i < d.N) tile[f][i] = d.Xaug[static_cast<int64_t>(f0 + f) * d.ldN + i0 + i];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 64 * 64; k += blockDim.x) {
+      const int i = k >> 6, f = k & 63;
+      if (f0 + f < d.p_aug && i0 + i < d.N) d.Xrow[static_cast<int64_t>(i0 + i) * d.ldP + f0 + f] = tile[f][i];
+    }
+    __syncthreads();
+  }
+}
+
 // flush_index of the iteration (Alg. 3): one keyed permutation of the rows,
 // shared by every feature and tree
 __global__ void k_permut_pi(Dev d) {
@@ -510,30 +539,33 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
     {
       const uint32_t i = oob[r];
       const uint32_t pi = d.piv[i];
+      const uint8_t* xi = d.Xrow + static_cast<int64_t>(i) * d.ldP;  // the row's bins, row-major
+      const uint8_t* xpi = d.Xrow + static_cast<int64_t>(pi) * d.ldP;  // the flush_index row's bins
       // the row's path: node, split word, and the row's own bin at each node;
       // the children's words are loaded with the bin (one round trip a level)
       uint32_t path[kMaxDepth], pw[kMaxDepth];
       uint8_t px[kMaxDepth];
       int depth = 0;
       uint32_t k = static_cast<uint32_t>(tau);
-      uint32_t s = d.nd_split[k], c = d.nd_child[k];
+      const uint2 root = d.nd_sc[k];
+      uint32_t s = root.x, c = root.y;
       while (depth < kMaxDepth && s != kLeaf) {
-        const uint8_t x = d.Xaug[static_cast<int64_t>(s >> 8) * d.ldN + i];
-        const uint32_t s0 = d.nd_split[c], s1 = d.nd_split[c + 1], c0 = d.nd_child[c], c1 = d.nd_child[c + 1];
+        const uint8_t x = xi[s >> 8];
+        const uint2 n0 = d.nd_sc[c], n1 = d.nd_sc[c + 1];
         path[depth] = k;
         pw[depth] = s;
         px[depth] = x;
         ++depth;
         const bool right = x > (s & 255u);
         k = c + (right ? 1u : 0u);
-        s = right ? s1 : s0;
-        c = right ? c1 : c0;
+        s = right ? n1.x : n0.x;
+        c = right ? n1.y : n0.y;
       }
       const uint32_t q = k;
       visits += static_cast<unsigned long long>(depth);
       // the permuted row's bins of every feature on the path, loaded together
       uint8_t xq[kMaxDepth];
-      for (int a = 0; a < depth; ++a) xq[a] = d.Xaug[static_cast<int64_t>(pw[a] >> 8) * d.ldN + pi];
+      for (int a = 0; a < depth; ++a) xq[a] = xpi[pw[a] >> 8];
       // the re-walks: for each distinct feature f on the path whose swapped
       // value sends the row the other way at some node testing f, the walk
       // restarts at that node's other child
@@ -570,14 +602,15 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
           if (w0 + u < nw) {
             // the other child of the node where the swapped value turns
             const uint32_t at = wstart[w0 + u];
-            wk[u] = d.nd_child[path[at >> 1]] + (at & 1u);
+            wk[u] = d.nd_sc[path[at >> 1]].y + (at & 1u);
           }
         }
 #pragma unroll
         for (int u = 0; u < kWalks; ++u)
           if (w0 + u < nw) {
-            ws[u] = d.nd_split[wk[u]];
-            wc[u] = d.nd_child[wk[u]];
+            const uint2 n = d.nd_sc[wk[u]];
+            ws[u] = n.x;
+            wc[u] = n.y;
           }
         for (int guard = 0; guard <= kMaxDepth; ++guard) {  // trees are at most kMaxDepth deep
           bool busy = false;
@@ -588,14 +621,13 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
             ++visits;
             const uint32_t fx = wfx[w0 + u];
             const uint32_t g = ws[u] >> 8;
-            const uint8_t x = (g == (fx >> 8)) ? static_cast<uint8_t>(fx & 255u)
-                                               : d.Xaug[static_cast<int64_t>(g) * d.ldN + i];
+            const uint8_t x = (g == (fx >> 8)) ? static_cast<uint8_t>(fx & 255u) : xi[g];
             const uint32_t c = wc[u];
-            const uint32_t s0 = d.nd_split[c], s1 = d.nd_split[c + 1], c0 = d.nd_child[c], c1 = d.nd_child[c + 1];
+            const uint2 n0 = d.nd_sc[c], n1 = d.nd_sc[c + 1];
             const bool right = x > (ws[u] & 255u);
             wk[u] = c + (right ? 1u : 0u);
-            ws[u] = right ? s1 : s0;
-            wc[u] = right ? c1 : c0;
+            ws[u] = right ? n1.x : n0.x;
+            wc[u] = right ? n1.y : n0.y;
           }
           if (!busy) break;
         }
@@ -636,6 +668,8 @@ __global__ void k_permut_final(Dev d) {
 
 void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
   k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
+  k_transpose_rows<<<grid, 256, 0, st>>>(d);
+  k_pack_nodes<<<grid, 256, 0, st>>>(d);
   k_permut<<<walk_grid, 128, 0, st>>>(d);
   k_permut_final<<<grid, 256, 0, st>>>(d);
 }
@@ -666,7 +700,7 @@ __device__ __forceinline__ uint32_t forest_walk(const Dev& d, int tau, uint32_t 
     const uint32_t s = d.nd_split[k];
     if (s == kLeaf) break;
     const uint32_t g = s >> 8;
-    const uint8_t x = d.Xaug[static_cast<int64_t>(g) * d.ldN + (g == f ? pi : i)];
+    const uint8_t x = d.Xrow[static_cast<int64_t>(g == f ? pi : i) * d.ldP + g];
     k = d.nd_child[k] + (x > (s & 255u) ? 1u : 0u);
   }
   return k;
@@ -718,7 +752,7 @@ __global__ void k_fperm_delta(Dev d, uint32_t r0, uint32_t rows) {
     int depth = 0;
     uint32_t k = static_cast<uint32_t>(tau);
     for (uint32_t s = d.nd_split[k]; s != kLeaf && depth < kMaxDepth; s = d.nd_split[k]) {
-      const uint8_t x = d.Xaug[static_cast<int64_t>(s >> 8) * d.ldN + i];
+      const uint8_t x = d.Xrow[static_cast<int64_t>(i) * d.ldP + (s >> 8)];
       pw[depth++] = s;
       k = d.nd_child[k] + (x > (s & 255u) ? 1u : 0u);
     }
@@ -791,6 +825,7 @@ __global__ void k_fperm_final(Dev d) {
 
 void launch_forest_permut(const Dev& d, int grid, cudaStream_t st) {
   k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
+  k_transpose_rows<<<grid, 256, 0, st>>>(d);
   cudaMemsetAsync(d.fbase, 0, static_cast<size_t>(d.N) * forest_k(d) * kCsaLimbs * sizeof(long long), st);
   k_fperm_base<<<grid, 256, 0, st>>>(d);
   k_fperm_base_mean<<<grid, 256, 0, st>>>(d);

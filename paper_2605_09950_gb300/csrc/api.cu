@@ -386,8 +386,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   // The limit is a property of the kernel, shared by every session in the
   // process: set it to what the variant can need at most (its largest class
   // count, 256 bins) so that no session lowers it below another's launches.
-  const int variant_C[4] = {2, 4, 8, 1};
-  const size_t smem_cap = std::max(s->split_smem, split_smem_bytes(d.kind, variant_C[variant], 256));
+  const size_t smem_cap = std::max(s->split_smem, split_smem_bytes(d.kind, variant_classes(variant), 256));
   for (int i = 0; i < nk; ++i)
     CK(cudaFuncSetAttribute(kptr[i], cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_cap)));
   int per_sm = 0;

@@ -113,6 +113,7 @@ void launch_split(const Dev& d, int level, int grid_small, int grid_big, uint64_
                   cudaEvent_t hist_end);
 size_t ninfo_bytes(int variant);
 int split_variant(int kind, int C);
+int variant_classes(int variant);  // largest class count of a kernel variant (1 for regression)
 void split_kernel_ptrs(int variant, const void** ptrs, int* n);  // kernels taking dynamic shared memory
 const void* small_kernel_ptr(int variant);  // for its occupancy
 size_t cand_bytes(int variant);
@@ -135,9 +136,10 @@ __host__ __device__ inline size_t hist_smem_per_warp(int kind, int C, int B) {
                              : static_cast<size_t>(hist_words_n(B)) * 4 + static_cast<size_t>(B + (B >> 3) + 1) * 8;
   return (b + 15) & ~static_cast<size_t>(15);
 }
-// per warp: the histogram, then a node's row entries (up to kRegRows)
+// per warp: the histogram, a node's row entries (up to kRegRows), then the
+// histogram's occupancy bitmap (256 bits and one spare word, padded to 48 B)
 __host__ __device__ inline size_t split_smem_per_warp(int kind, int C, int B) {
-  return hist_smem_per_warp(kind, C, B) + kRegRows * 4;
+  return hist_smem_per_warp(kind, C, B) + kRegRows * 4 + 48;
 }
 __host__ __device__ inline size_t split_smem_bytes(int kind, int C, int B) {
   return (kSplitThreads / 32) * split_smem_per_warp(kind, C, B);

@@ -30,6 +30,7 @@
 // float pre-screen; equal scores go to the lower key = (feature index, or
 // the draw slot with tie_break = 1) << 8 | bin.
 #include <cstdint>
+#include <type_traits>
 
 #include "engine.cuh"
 
@@ -54,6 +55,14 @@ namespace {
 constexpr int kSmallAhead = BORUTA_SMALL_AHEAD;
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Class count of a variant: the kernels are instantiated with CM = 3, 4 and 5
+// for exactly that many classes (their class loops then unroll to the real
+// count), CM = 2 for one or two classes and CM = 8 for six to eight.
+template <int CM>
+__device__ __forceinline__ int ncls(const Dev& d) {
+  return (CM == 3 || CM == 4 || CM == 5) ? CM : d.C;
+}
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -278,7 +287,7 @@ template <int KIND, int CM>
 __device__ uint32_t commit_split(const Dev& d, uint32_t k, const Cand<CM>& b, const NodeInfo<CM>& nd) {
   double delta = 0.0;
   uint32_t sp = kLeaf;
-  if (b.valid && split_delta<KIND, CM>(b, nd, d.C, d.precision, &delta)) {
+  if (b.valid && split_delta<KIND, CM>(b, nd, ncls<CM>(d), d.precision, &delta)) {
     sp = (static_cast<uint32_t>(b.feat) << 8) | static_cast<uint32_t>(b.bin);
     d.nd_delta[k] = delta;
     d.nd_ln[k] = b.nL;
@@ -287,7 +296,7 @@ __device__ uint32_t commit_split(const Dev& d, uint32_t k, const Cand<CM>& b, co
     } else {
 #pragma unroll
       for (int c = 0; c < CM; ++c)
-        if (c < d.C) d.nd_lcnt[static_cast<int64_t>(k) * d.C + c] = b.cL[c];
+        if (c < ncls<CM>(d)) d.nd_lcnt[static_cast<int64_t>(k) * d.C + c] = b.cL[c];
     }
     if (!d.permut) {  // Alg. 2: this node's gain x samples, summed exactly per (tree, feature)
       if (!csa_add(d.acc + (static_cast<int64_t>(d.nd_tree[k]) * d.p_aug + b.feat) * kCsaLimbs, delta))
@@ -527,7 +536,7 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
   const uint32_t* rows_in = d.rows[level & 1];
   uint32_t* rows_out = d.rows[(level & 1) ^ 1];
   const uint32_t ns_nodes = d.nsmall[level];
-  const int C = d.C;
+  const int C = ncls<CM>(d);
   unsigned long long bytes = 0;
   for (uint32_t idx = gwarp; idx < ns_nodes; idx += nwarps) {
     const uint32_t k = d.small[idx];
@@ -782,10 +791,13 @@ __device__ __forceinline__ void screen_keep(Screen<CM>& S, float sc, int bb, uin
   }
 }
 
+// occ: the lane's bins that may be non-empty (bit q: bin b0 + q); the others
+// are known to be empty and are not read.
 template <int KIND, int CM>
-__device__ __forceinline__ void scan_screen(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, Screen<CM>& S) {
+__device__ __forceinline__ void scan_screen(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, Screen<CM>& S,
+                                            uint32_t occ = 0xFFu) {
   const int lane = threadIdx.x & 31;
-  const int C = d.C, B = d.B;
+  const int C = ncls<CM>(d), B = d.B;
   const int bpl = (B + 31) >> 5;  // bins per lane (<= 8)
   const int b0 = lane * bpl;
   S.mask = 0u;
@@ -802,7 +814,8 @@ __device__ __forceinline__ void scan_screen(const Dev& d, const NodeInfo<CM>& nd
       S.pre[k] = 0u;
       S.cb[k] = 0u;
     }
-    for (int q = 0; q < bpl; ++q) {
+    for (uint32_t m = occ & ((1u << bpl) - 1u); m; m &= m - 1) {
+      const int q = __ffs(m) - 1;
       const int bb = b0 + q;
       if (bb < B) {
         uint32_t wb = 0;
@@ -839,7 +852,8 @@ __device__ __forceinline__ void scan_screen(const Dev& d, const NodeInfo<CM>& nd
     long long ts = 0;
 #pragma unroll
     for (int k = 0; k < CM; ++k) S.cb[k] = 0u;
-    for (int q = 0; q < bpl; ++q) {
+    for (uint32_t m = occ & ((1u << bpl) - 1u); m; m &= m - 1) {
+      const int q = __ffs(m) - 1;
       const int bb = b0 + q;
       if (bb < B) {
         const uint32_t h = hn[bb + (bb >> 3)];
@@ -867,7 +881,7 @@ template <int KIND, int CM>
 __device__ void scan_exact(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, const Screen<CM>& S, float thr,
                            int feat, uint32_t tkey, Cand<CM>& out) {
   const int lane = threadIdx.x & 31;
-  const int C = d.C, B = d.B;
+  const int C = ncls<CM>(d), B = d.B;
   const int b0 = lane * ((B + 31) >> 5);
   Cand<CM> mine;
   mine.valid = false;
@@ -997,10 +1011,11 @@ __device__ __forceinline__ void unpack_cand(const PackedCand<CM>& p, const NodeI
 // best and is packed as is; otherwise the candidates inside the window are
 // compared exactly.
 template <int KIND, int CM>
-__device__ void scan_pack(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, uint32_t f, PackedCand<CM>* dst) {
+__device__ void scan_pack(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, uint32_t f, PackedCand<CM>* dst,
+                          uint32_t occ = 0xFFu) {
   const int lane = threadIdx.x & 31;
   Screen<CM> S;
-  scan_screen<KIND, CM>(d, nd, hw, S);
+  scan_screen<KIND, CM>(d, nd, hw, S, occ);
   const float mx = warp_max_f(S.lmax);
   if (mx < 0.0f) {
     if (lane == 0) {
@@ -1039,11 +1054,14 @@ __device__ void scan_pack(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* 
 // Histogram of one feature over a node of at most kRegRows rows whose entries
 // are staged in the warp's shared memory (ebuf), the feature's bins already
 // gathered into b (lane l holds rows q * 32 + l).
+// The histogram is all zero on entry (the staged path leaves it so, see
+// hist_unstage); the bins that receive rows are marked in occ.
 template <int KIND>
 __device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const uint32_t* ebuf,
-                                            const uint32_t (&b)[kRegRows / 32], uint32_t* hw) {
+                                            const uint32_t (&b)[kRegRows / 32], uint32_t* hw, uint32_t* occ) {
   const int lane = threadIdx.x & 31;
   if (regs4(d, KIND)) {
+    if (lane == 0) occ[0] = (1u << d.B) - 1u;  // regs4_store writes bins 0..B-1
     uint32_t c0[4] = {0u, 0u, 0u, 0u}, c1[4] = {0u, 0u, 0u, 0u};
     long long sy[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -1056,8 +1074,6 @@ __device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const ui
     regs4_store<KIND>(d, hw, c0, c1, sy);
     return;
   }
-  hist_clear<KIND>(d, hw);
-  __syncwarp();
   if (KIND == 0) {
 #pragma unroll
     for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) {
@@ -1065,6 +1081,7 @@ __device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const ui
       if (r < len) {
         const uint32_t e = ebuf[r];
         atomicAdd(&hw[b[q] * d.C + ent_y(e) + (b[q] >> 3)], ent_w<0>(e));
+        atomicOr(&occ[b[q] >> 5], 1u << (b[q] & 31u));
       }
     }
   } else {
@@ -1079,9 +1096,39 @@ __device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const ui
         const long long yq = d.yreg[e >> 8];
         atomicAdd(&hn[b[q] + (b[q] >> 3)], w);
         atomicAdd(&hs[b[q] + (b[q] >> 3)], static_cast<unsigned long long>(static_cast<long long>(w) * yq));
+        atomicOr(&occ[b[q] >> 5], 1u << (b[q] & 31u));
       }
     }
   }
+  __syncwarp();
+}
+
+// The lane's bits of the occupancy bitmap: its bins b0 .. b0 + bpl - 1.
+__device__ __forceinline__ uint32_t lane_occ(const Dev& d, const uint32_t* occ) {
+  const int bpl = (d.B + 31) >> 5;
+  const int b0 = (threadIdx.x & 31) * bpl;
+  const uint64_t w = static_cast<uint64_t>(occ[b0 >> 5]) | (static_cast<uint64_t>(occ[(b0 >> 5) + 1]) << 32);
+  return static_cast<uint32_t>(w >> (b0 & 31)) & ((1u << bpl) - 1u);
+}
+
+// Zeroes the occupied bins of a staged histogram (each lane its own, after
+// its own reads) and the bitmap, so that the next feature starts from zero.
+template <int KIND>
+__device__ __forceinline__ void hist_unstage(const Dev& d, uint32_t* hw, uint32_t* occ, uint32_t mine) {
+  const int lane = threadIdx.x & 31;
+  const int bpl = (d.B + 31) >> 5;
+  const int b0 = lane * bpl;
+  for (uint32_t m = mine; m; m &= m - 1) {
+    const int bb = b0 + __ffs(m) - 1;
+    if (KIND == 0) {
+      for (int k = 0; k < d.C; ++k) hw[bb * d.C + k + (bb >> 3)] = 0u;
+    } else {
+      hw[bb + (bb >> 3)] = 0u;
+      reinterpret_cast<unsigned long long*>(hw + hist_words_n(d.B))[bb + (bb >> 3)] = 0ull;
+    }
+  }
+  __syncwarp();
+  if (lane < 9) occ[lane] = 0u;
   __syncwarp();
 }
 
@@ -1257,7 +1304,11 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
   uint32_t* ebuf = hw + hist_smem_per_warp(d.kind, d.C, d.B) / 4;
+  uint32_t* occ = ebuf + kRegRows;
   if (chunk_nodes(d, level) == 0u) return;
+  hist_clear<KIND>(d, hw);  // from here on a feature leaves the histogram zeroed
+  if (lane < 9) occ[lane] = 0u;
+  __syncwarp();
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
@@ -1295,11 +1346,16 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
         if (j + 1 < count)
           gather_staged(column(d, static_cast<uint32_t>(__shfl_sync(kFull, chunk, (j + 1) & 31) & 0x3FFFFFu)),
                         nd.len, ebuf, bn);
-        hist_staged<KIND>(d, nd.len, ebuf, b, hw);
+        hist_staged<KIND>(d, nd.len, ebuf, b, hw, occ);
+        const uint32_t mine = lane_occ(d, occ);
+        scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu), mine);
+        hist_unstage<KIND>(d, hw, occ, mine);
       } else {
         build_hist<KIND>(d, nd.base, nd.len, rows_in, column(d, f), hw);
+        scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu));
+        hist_clear<KIND>(d, hw);
+        __syncwarp();
       }
-      scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu));
     }
     __syncwarp();  // the entry buffer is reused by the next group
     // algorithmic bytes (the method's per-level figure): one bin per row and
@@ -1330,7 +1386,7 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize_band(Dev d,
     // float screen over the per-feature bests, then the exact argmax among
     // those inside the window
     float lmax = -1.0f;
-    for (int s = lane; s < d.mtry; s += 32) lmax = fmaxf(lmax, packed_score_f<KIND, CM>(pc[s], nd, d.C));
+    for (int s = lane; s < d.mtry; s += 32) lmax = fmaxf(lmax, packed_score_f<KIND, CM>(pc[s], nd, ncls<CM>(d)));
     const float mx = warp_max_f(lmax);
     const float thr = screen(mx);
     Cand<CM> best;
@@ -1341,9 +1397,9 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize_band(Dev d,
       mine.valid = false;
       if (s < d.mtry) {
         const PackedCand<CM> p = pc[s];
-        if (packed_score_f<KIND, CM>(p, nd, d.C) >= thr) {
+        if (packed_score_f<KIND, CM>(p, nd, ncls<CM>(d)) >= thr) {
           const uint32_t tkey = d.tie_break == 1 ? static_cast<uint32_t>(s) : (p.fb >> 8);
-          unpack_cand<KIND, CM>(p, nd, d.C, tkey, mine);
+          unpack_cand<KIND, CM>(p, nd, ncls<CM>(d), tkey, mine);
         }
       }
       if (__ballot_sync(kFull, mine.valid) == 0u) continue;
@@ -1479,83 +1535,65 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, uint6
   cudaStreamWaitEvent(st, join, 0);
 }
 
+// Kernel variants: 0..4 classification with CM = 2, 3, 4, 5, 8 classes at
+// most (3, 4 and 5 exactly), 5 regression.
+template <typename F>
+auto with_variant(int variant, F&& f) {
+  switch (variant) {
+    case 0: return f(std::integral_constant<int, 0>{}, std::integral_constant<int, 2>{});
+    case 1: return f(std::integral_constant<int, 0>{}, std::integral_constant<int, 3>{});
+    case 2: return f(std::integral_constant<int, 0>{}, std::integral_constant<int, 4>{});
+    case 3: return f(std::integral_constant<int, 0>{}, std::integral_constant<int, 5>{});
+    case 4: return f(std::integral_constant<int, 0>{}, std::integral_constant<int, 8>{});
+    default: return f(std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{});
+  }
+}
+
 }  // namespace
 
 int split_variant(int kind, int C) {
-  if (kind != 0) return 3;
-  return C <= 2 ? 0 : (C <= 4 ? 1 : 2);
+  if (kind != 0) return 5;
+  return C <= 2 ? 0 : (C <= 5 ? C - 2 : 4);
 }
 
+int variant_classes(int variant) { return with_variant(variant, [](auto, auto cm) { return decltype(cm)::value; }); }
+
 size_t packed_bytes(int variant) {
-  switch (variant) {
-    case 0: return sizeof(PackedCand<2>);
-    case 1: return sizeof(PackedCand<4>);
-    case 2: return sizeof(PackedCand<8>);
-    default: return sizeof(PackedCand<1>);
-  }
+  return with_variant(variant, [](auto, auto cm) { return sizeof(PackedCand<decltype(cm)::value>); });
 }
 
 size_t cand_bytes(int variant) {
-  switch (variant) {
-    case 0: return sizeof(Cand<2>);
-    case 1: return sizeof(Cand<4>);
-    case 2: return sizeof(Cand<8>);
-    default: return sizeof(Cand<1>);
-  }
+  return with_variant(variant, [](auto, auto cm) { return sizeof(Cand<decltype(cm)::value>); });
+}
+
+size_t ninfo_bytes(int variant) {
+  return with_variant(variant, [](auto, auto cm) { return sizeof(NodeInfo<decltype(cm)::value>); });
 }
 
 void split_kernel_ptrs(int variant, const void** ptrs, int* n) {
-  int i = 0;
-  switch (variant) {
-    case 0:
-      ptrs[i++] = reinterpret_cast<const void*>(&k_items<0, 2>);
-      ptrs[i++] = reinterpret_cast<const void*>(&k_items_band<0, 2>);
-      break;
-    case 1:
-      ptrs[i++] = reinterpret_cast<const void*>(&k_items<0, 4>);
-      ptrs[i++] = reinterpret_cast<const void*>(&k_items_band<0, 4>);
-      break;
-    case 2:
-      ptrs[i++] = reinterpret_cast<const void*>(&k_items<0, 8>);
-      ptrs[i++] = reinterpret_cast<const void*>(&k_items_band<0, 8>);
-      break;
-    default:
-      ptrs[i++] = reinterpret_cast<const void*>(&k_items<1, 1>);
-      ptrs[i++] = reinterpret_cast<const void*>(&k_items_band<1, 1>);
-      break;
-  }
-  *n = i;
+  with_variant(variant, [&](auto kind, auto cm) {
+    constexpr int K = decltype(kind)::value, CM = decltype(cm)::value;
+    ptrs[0] = reinterpret_cast<const void*>(&k_items<K, CM>);
+    ptrs[1] = reinterpret_cast<const void*>(&k_items_band<K, CM>);
+    return 0;
+  });
+  *n = 2;
 }
 
 const void* small_kernel_ptr(int variant) {
-  switch (variant) {
-    case 0: return reinterpret_cast<const void*>(&k_split_small<0, 2>);
-    case 1: return reinterpret_cast<const void*>(&k_split_small<0, 4>);
-    case 2: return reinterpret_cast<const void*>(&k_split_small<0, 8>);
-    default: return reinterpret_cast<const void*>(&k_split_small<1, 1>);
-  }
+  return with_variant(variant, [](auto kind, auto cm) {
+    return reinterpret_cast<const void*>(&k_split_small<decltype(kind)::value, decltype(cm)::value>);
+  });
 }
 
 void launch_split(const Dev& d, int level, int grid_small, int grid_big, uint64_t big_bound, size_t smem,
                   cudaStream_t st, cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hs,
                   cudaEvent_t he) {
-  switch (split_variant(d.kind, d.C)) {
-    case 0: launch_level<0, 2>(d, level, grid_small, grid_big, big_bound, smem, st, st2, fork, join, hs, he); break;
-    case 1: launch_level<0, 4>(d, level, grid_small, grid_big, big_bound, smem, st, st2, fork, join, hs, he); break;
-    case 2: launch_level<0, 8>(d, level, grid_small, grid_big, big_bound, smem, st, st2, fork, join, hs, he); break;
-    default:
-      launch_level<1, 1>(d, level, grid_small, grid_big, big_bound, smem, st, st2, fork, join, hs, he);
-      break;
-  }
-}
-
-size_t ninfo_bytes(int variant) {
-  switch (variant) {
-    case 0: return sizeof(NodeInfo<2>);
-    case 1: return sizeof(NodeInfo<4>);
-    case 2: return sizeof(NodeInfo<8>);
-    default: return sizeof(NodeInfo<1>);
-  }
+  with_variant(split_variant(d.kind, d.C), [&](auto kind, auto cm) {
+    launch_level<decltype(kind)::value, decltype(cm)::value>(d, level, grid_small, grid_big, big_bound, smem, st,
+                                                              st2, fork, join, hs, he);
+    return 0;
+  });
 }
 
 }  // namespace bgb

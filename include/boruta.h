@@ -83,6 +83,12 @@ typedef struct {
                       whatever `precision` says */
   int forest_rows; /* permut_form = 1: rows per block of the (row, column) accumulators (0 = as
                       many as fit in about 1 GiB, the default); results are identical */
+  int autotune;    /* 1: the first step of a session (of every job of a batch) times its
+                      iteration once per histogram tile shape -- column bytes per feature band
+                      (12, 24, 48 MiB) x row-feature work per group of a larger node (4096, 8192,
+                      16384) -- restoring the state after each, and keeps the fastest; results
+                      are identical for every shape (boruta_session_tuning reports the
+                      timings).  0 (default): 24 MiB, 8192. */
 } boruta_opts;
 
 /* Host-side, caller-allocated outputs. */
@@ -238,6 +244,14 @@ int boruta_session_dump(boruta_session* s, int what, void* host, int64_t capacit
  *                        state once per node, partition traffic). */
 int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* launches, double* hist_bytes,
                                 double* split_ms, double* split_bytes);
+
+/* The autotuner's measurements (opts->autotune = 1): *n_tried candidates, of
+ * which the first `capacity` are written (any pointer may be NULL): the
+ * row-feature work per group, the column bytes per band, and the
+ * milliseconds of the timed iteration; *chosen is the index kept (-1 before
+ * the first step or without autotune). */
+int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried, uint32_t* group_work,
+                          int64_t* band_bytes, double* ms, int32_t* chosen);
 
 /* Timing of the last step's importance stage (Alg. 2 normalisation, or the
  * Alg. 3 tree walks and their reduction), from CUDA events on the session's

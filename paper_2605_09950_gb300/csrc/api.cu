@@ -58,6 +58,14 @@ struct boruta_session {
   cudaStream_t st = nullptr;
   int64_t p = 0, N = 0;
   int task = 0, mtry_opt = 0, max_iter = 0, t = 0, split_path = 0, chunk_nodes = 0;
+  // histogram tile shape: column bytes per feature band and row x feature
+  // work per group; opts.autotune times the candidates on the first step
+  int64_t band_bytes = kBandBytes;
+  bool autotune = false, tuned = false;
+  std::vector<uint32_t> tune_gw;
+  std::vector<int64_t> tune_bb;
+  std::vector<double> tune_ms;
+  int tune_chosen = -1;
   int pending_t = 0;  // iteration enqueued and not yet finished
   bool graph = false;                   // iterations replayed through an instantiated CUDA graph
   cudaStream_t gst = nullptr;           // capture stream of the graph
@@ -152,6 +160,7 @@ static int check_args(const uint8_t* X, int64_t ld, const void* y, int64_t N, in
   if (o->chunk_nodes < 0) return fail(BORUTA_EINVAL, "opts: chunk_nodes must not be negative");
   if (o->permut_form < 0 || o->permut_form > 1) return fail(BORUTA_EINVAL, "opts: permut_form takes 0 or 1");
   if (o->forest_rows < 0) return fail(BORUTA_EINVAL, "opts: forest_rows must not be negative");
+  if (o->autotune < 0 || o->autotune > 1) return fail(BORUTA_EINVAL, "opts: autotune takes 0 or 1");
   if (o->permut_form == 1 && !(task & BORUTA_PERMUT))
     return fail(BORUTA_EINVAL, "opts: permut_form = 1 is a form of Alg. 3 (task needs BORUTA_PERMUT)");
   if (o->precision < 0 || o->precision > 1 || o->tie_break < 0 || o->tie_break > 1 || o->stat < 0 ||
@@ -181,6 +190,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->mtry_opt = mtry;
   s->split_path = o->split_path;
   s->chunk_nodes = o->chunk_nodes;
+  s->autotune = o->autotune != 0;
   s->graph = o->graph != 0;
   s->max_iter = max_iter;
   Dev& d = s->d;
@@ -195,6 +205,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   d.M = n_trees;
   d.max_iter = max_iter;
   d.precision = o->precision;
+  d.group_work = kGroupWork;
   d.permut_form = d.permut ? o->permut_form : 0;
   d.tie_break = o->tie_break;
   d.stat = o->stat;
@@ -468,7 +479,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   d.chunk_cap = static_cast<uint32_t>(std::min<uint64_t>(d.item_cap / static_cast<uint64_t>(d.mtry), 1u << 26));
   if (s->chunk_nodes > 0) d.chunk_cap = std::min<uint32_t>(d.chunk_cap, static_cast<uint32_t>(s->chunk_nodes));
   if (s->split_path == 0 && d.chunk_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
-    int64_t w = std::max<int64_t>(1, kBandBytes / d.ldN);
+    int64_t w = std::max<int64_t>(1, s->band_bytes / d.ldN);
     w = std::max<int64_t>(w, (p_aug + kMaxBands - 1) / kMaxBands);
     d.band_w = static_cast<int32_t>(w);
     d.nbands = static_cast<int32_t>((p_aug + w - 1) / w);
@@ -536,10 +547,72 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   return 0;
 }
 
+static int step_finish(boruta_session* s, int32_t* undecided);
+
+// Histogram tile shape by measurement: the next iteration is run once per
+// candidate (column bytes per feature band x row-feature work per group),
+// timed with CUDA events, and the state is restored after each run; the
+// fastest candidate is kept.  The candidates give identical results (the
+// shape decides only which warp does which part of the same sums).
+static int tune_tiles(boruta_session* s) {
+  static const uint32_t kGw[] = {4096u, 8192u, 16384u};
+  static const int64_t kBb[] = {int64_t{12} << 20, int64_t{24} << 20, int64_t{48} << 20};
+  const int64_t p = s->p, T = s->max_iter;
+  std::vector<int8_t> dec(p);
+  std::vector<int32_t> hits(p);
+  std::vector<double> hist(static_cast<size_t>(T * p)), smax(T);
+  int32_t t0 = 0;
+  int rc = boruta_session_read(s, dec.data(), hits.data(), hist.data(), smax.data(), &t0);
+  if (rc) return rc;
+  cudaEvent_t e[2];
+  CK(cudaEventCreate(&e[0]));
+  CK(cudaEventCreate(&e[1]));
+  s->tune_gw.clear();
+  s->tune_bb.clear();
+  s->tune_ms.clear();
+  const bool graph = s->graph;
+  s->graph = false;
+  for (uint32_t gw : kGw)
+    for (int64_t bb : kBb) {
+      s->d.group_work = gw;
+      s->band_bytes = bb;
+      CK(cudaEventRecord(e[0], s->st));
+      rc = enqueue_iteration(s, t0 + 1, s->st);
+      if (!rc) {
+        s->pending_t = t0 + 1;
+        CK(cudaEventRecord(e[1], s->st));
+        rc = step_finish(s, nullptr);
+      }
+      float ms = 0.f;
+      if (!rc) CK(cudaEventElapsedTime(&ms, e[0], e[1]));
+      if (!rc) rc = boruta_session_write(s, dec.data(), hits.data(), hist.data(), smax.data(), t0);
+      if (rc) break;
+      s->tune_gw.push_back(gw);
+      s->tune_bb.push_back(bb);
+      s->tune_ms.push_back(ms);
+    }
+  cudaEventDestroy(e[0]);
+  cudaEventDestroy(e[1]);
+  s->graph = graph;
+  if (rc) return rc;
+  size_t best = 0;
+  for (size_t i = 1; i < s->tune_ms.size(); ++i)
+    if (s->tune_ms[i] < s->tune_ms[best]) best = i;
+  s->d.group_work = s->tune_gw[best];
+  s->band_bytes = s->tune_bb[best];
+  s->tune_chosen = static_cast<int>(best);
+  return 0;
+}
+
 static int step_launch(boruta_session* s) {
   if (!s) return fail(BORUTA_EINVAL, "session is NULL");
   if (s->finished) return fail(BORUTA_EINVAL, "the run is finished (no undecided feature or t = max_iter)");
   if (s->pending_t) return fail(BORUTA_EINVAL, "an iteration is already in flight");
+  if (s->autotune && !s->tuned) {
+    s->tuned = true;
+    const int rc = tune_tiles(s);
+    if (rc) return rc;
+  }
   const int t = s->t + 1;
   if (!s->graph) {
     const int rc = enqueue_iteration(s, t, s->st);
@@ -690,6 +763,20 @@ int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* lau
   if (hist_bytes) *hist_bytes = s->hist_bytes;
   if (split_ms) *split_ms = s->split_ms;
   if (split_bytes) *split_bytes = s->split_bytes;
+  return 0;
+}
+
+int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried, uint32_t* group_work,
+                          int64_t* band_bytes, double* ms, int32_t* chosen) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  const int n = static_cast<int>(s->tune_ms.size());
+  if (n_tried) *n_tried = n;
+  if (chosen) *chosen = s->tune_chosen;
+  for (int i = 0; i < n && i < capacity; ++i) {
+    if (group_work) group_work[i] = s->tune_gw[i];
+    if (band_bytes) band_bytes[i] = s->tune_bb[i];
+    if (ms) ms[i] = s->tune_ms[i];
+  }
   return 0;
 }
 

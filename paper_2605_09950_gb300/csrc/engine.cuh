@@ -62,6 +62,7 @@ struct Dev {
   uint32_t* band_cnt;            // [kMaxBands + 1] groups per band, then cursors; last: total
   uint64_t item_cap;
   int32_t band_w, nbands;        // columns per band (0: grouped path only), bands
+  uint32_t group_work;           // row x feature work per group of a larger node (tile shape)
   uint32_t chunk0, chunk_cap;    // band path: first larger node of the chunk, nodes per chunk
   // ---- importance and Boruta state
   long long* acc;                // [M][p_aug][kCsaLimbs] exact per-tree accumulators (carry-save)
@@ -94,7 +95,7 @@ constexpr int kMaxIterations = 126;          // max_iter limit (exact binomial t
 #define BORUTA_STAGED_ROWS 128
 #endif
 constexpr uint32_t kRegRows = BORUTA_STAGED_ROWS;  // node rows a warp stages in shared memory
-constexpr uint32_t kGroupWork = 8192;        // row x feature work per group for larger nodes
+constexpr uint32_t kGroupWork = 8192;        // default row x feature work per group for larger nodes
 // row state the method moves per row and tree level besides the bins: the
 // row's entry read and rewritten by the partition (4 + 4 B), its weight and
 // label (1 + 1 B), or weight and 8-byte fixed-point target (regression)

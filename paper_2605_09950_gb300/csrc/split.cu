@@ -1172,8 +1172,8 @@ __device__ __forceinline__ uint64_t pack_group(uint32_t rank, uint32_t first, ui
 }
 
 // most items in a group of a node with len rows
-__device__ __forceinline__ uint32_t group_cap(uint32_t len) {
-  return len <= kRegRows ? (1u << 14) : max(1u, kGroupWork / len);
+__device__ __forceinline__ uint32_t group_cap(const Dev& d, uint32_t len) {
+  return len <= kRegRows ? (1u << 14) : max(1u, d.group_work / len);
 }
 
 // Exclusive scan of a warp's per-band counters in place; returns the total.
@@ -1229,7 +1229,7 @@ __global__ void __launch_bounds__(256) k_plan_gen(Dev d, int level) {
     node_perm(d, k, P);
     for (int s = lane; s < d.mtry; s += 32) atomicAdd(&cnt[perm_apply(P, static_cast<uint32_t>(s)) / bw], 1u);
     __syncwarp();
-    const uint32_t gc = group_cap(len);
+    const uint32_t gc = group_cap(d, len);
     for (int b = lane; b < d.nbands; b += 32)
       if (cnt[b]) atomicAdd(&sband[b], (cnt[b] + gc - 1) / gc);
     __syncwarp();
@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(256) k_plan_scatter(Dev d, int level) {
     }
     __syncwarp();
     warp_scan_bands(cnt, d.nbands, lane);
-    const uint32_t gc = group_cap(len);
+    const uint32_t gc = group_cap(d, len);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int b = lane * bpl + q;

@@ -274,6 +274,40 @@ def test_graph_replay_matches_stream_launches(importance):
         np.testing.assert_array_equal(a[key], b[key], err_msg=key)
 
 
+@pytest.mark.parametrize("importance", [synth.TREEIMP, synth.PERMUT])
+def test_autotuned_tiles_give_the_same_run(importance):
+    """opts.autotune = 1: the first step times the nine histogram tile shapes
+    (band bytes x group work) on iteration 1, restoring the state after each,
+    and keeps the fastest; the run is the same, bit for bit, as with the
+    default shape, and the batched form with autotune equals it too."""
+    import torch
+
+    from paper_2605_09950_gb300 import boruta
+
+    w = synth.binary_small(N=900, p=20, n_inf=4, n_trees=16, max_depth=8, max_iter=6, importance=importance)
+    A = session(w)
+    B = session(w, autotune=1)
+    for _ in range(w.max_iter):
+        ua, ub = A.step(), B.step()
+        assert ua == ub
+        if ua == 0:
+            break
+    ra, rb = A.read(), B.read()
+    for key in ("decision", "hits", "imp_history", "shadow_max", "iterations"):
+        np.testing.assert_array_equal(ra[key], rb[key], err_msg=key)
+    tried, chosen = B.tuning()
+    assert len(tried) == 9 and 0 <= chosen < 9 and all(ms > 0 for _, _, ms in tried)
+    assert {gw for gw, _, _ in tried} == {4096, 8192, 16384}
+    assert A.tuning() == ([], -1)
+    params = w.params()
+    job = dict(X=torch.from_numpy(w.X).cuda(), y=torch.from_numpy(w.y).cuda(), N=w.N, **params)
+    outs = boruta.boruta_fit_batch([job, job], autotune=1)
+    plain = boruta.boruta_fit_batch([job, job])
+    for a, b in zip(outs, plain):
+        for key in ("decision", "hits", "imp_history", "shadow_max"):
+            np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
 def test_checkpoint_resume_is_exact():
     """Counter-based randomness: resuming from a state read at t = 4
     reproduces the uninterrupted run bit for bit."""

@@ -74,6 +74,25 @@ __device__ __forceinline__ const uint8_t* column(const Dev& d, uint32_t f) {
   return d.Xaug + static_cast<int64_t>(f) * d.ldN;
 }
 
+// L2 residency in the histogram kernels.  The bins are gathered band by band
+// (the groups are sorted by feature band), and a band's columns must stay in
+// L2 while its groups run; the nodes' row entries, streamed once per feature
+// group, would otherwise push them out.  So the gathers carry an evict-last
+// policy and the entry reads are streaming (evict-first) loads.
+__device__ __forceinline__ uint64_t keep_policy() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint32_t ld_keep(const uint8_t* a, uint64_t pol) {
+  uint32_t v;
+  asm("ld.global.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* a) { return __ldcs(a); }
+
 // Row entries: row << 8 | low byte.  Classification: low byte = y << 5 | w
 // (label < 8, bootstrap count < 32); regression: low byte = w (< 256).
 template <int KIND>
@@ -680,10 +699,11 @@ __device__ __forceinline__ void hist_add(const Dev& d, uint32_t r0, uint32_t len
   const int lane = threadIdx.x & 31;
   const int C = d.C, B = d.B;
   uint32_t b[kBatch];
+  const uint64_t pol = keep_policy();
 #pragma unroll
   for (int q = 0; q < kBatch; ++q) {
     const uint32_t r = r0 + q * 32 + lane;
-    b[q] = r < len ? col[e[q] >> 8] : 0u;
+    b[q] = r < len ? ld_keep(col + (e[q] >> 8), pol) : 0u;
   }
   if (KIND == 0) {
 #pragma unroll
@@ -711,7 +731,8 @@ __device__ __forceinline__ void hist_add(const Dev& d, uint32_t r0, uint32_t len
 // Warp-private histogram of one feature over a node's rows.  Rows are
 // gathered BORUTA_STREAM_BATCH per lane per pass so that as many independent
 // loads per lane are in flight.
-template <int KIND>
+// kClear: clear the histogram first (false: it is known to be zero).
+template <int KIND, bool kClear = true>
 __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint32_t* rows, const uint8_t* col,
                            uint32_t* hw) {
   const int lane = threadIdx.x & 31;
@@ -719,15 +740,16 @@ __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint3
   if (regs4(d, KIND)) {
     uint32_t c0[4] = {0u, 0u, 0u, 0u}, c1[4] = {0u, 0u, 0u, 0u};
     long long sy[4] = {0, 0, 0, 0};
+    const uint64_t pol = keep_policy();
     for (uint32_t r0 = 0; r0 < len; r0 += 32 * kBatch) {
       uint32_t e[kBatch], b[kBatch];
 #pragma unroll
       for (int q = 0; q < kBatch; ++q) {
         const uint32_t r = r0 + q * 32 + lane;
-        e[q] = r < len ? rows[base + r] : 0u;
+        e[q] = r < len ? ld_stream(rows + base + r) : 0u;
       }
 #pragma unroll
-      for (int q = 0; q < kBatch; ++q) b[q] = r0 + q * 32 + lane < len ? col[e[q] >> 8] : 0u;
+      for (int q = 0; q < kBatch; ++q) b[q] = r0 + q * 32 + lane < len ? ld_keep(col + (e[q] >> 8), pol) : 0u;
 #pragma unroll
       for (int q = 0; q < kBatch; ++q) {
         const bool v = r0 + q * 32 + lane < len;
@@ -737,12 +759,12 @@ __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint3
     regs4_store<KIND>(d, hw, c0, c1, sy);
     return;
   }
-  hist_clear<KIND>(d, hw);
+  if (kClear) hist_clear<KIND>(d, hw);
   uint32_t e[kBatch];
 #pragma unroll
   for (int q = 0; q < kBatch; ++q) {
     const uint32_t r = q * 32 + lane;
-    e[q] = r < len ? rows[base + r] : 0u;
+    e[q] = r < len ? ld_stream(rows + base + r) : 0u;
   }
   __syncwarp();
   for (uint32_t r0 = 0; r0 < len; r0 += 32 * kBatch) {
@@ -750,7 +772,7 @@ __device__ void build_hist(const Dev& d, int64_t base, uint32_t len, const uint3
 #pragma unroll
       for (int q = 0; q < kBatch; ++q) {
         const uint32_t r = r0 + q * 32 + lane;
-        e[q] = r < len ? rows[base + r] : 0u;
+        e[q] = r < len ? ld_stream(rows + base + r) : 0u;
       }
     }
     hist_add<KIND, kBatch>(d, r0, len, e, col, hw);
@@ -1135,10 +1157,11 @@ __device__ __forceinline__ void hist_unstage(const Dev& d, uint32_t* hw, uint32_
 __device__ __forceinline__ void gather_staged(const uint8_t* col, uint32_t len, const uint32_t* ebuf,
                                               uint32_t (&b)[kRegRows / 32]) {
   const int lane = threadIdx.x & 31;
+  const uint64_t pol = keep_policy();
 #pragma unroll
   for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) {
     const uint32_t r = q * 32 + lane;
-    b[q] = r < len ? col[ebuf[r] >> 8] : 0u;
+    b[q] = r < len ? ld_keep(col + (ebuf[r] >> 8), pol) : 0u;
   }
 }
 
@@ -1328,7 +1351,7 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
     // scanned.  Larger nodes stream their entries per feature.
     const bool staged = nd.len <= kRegRows;
     if (staged) {
-      for (uint32_t r = lane; r < nd.len; r += 32) ebuf[r] = rows_in[nd.base + r];
+      for (uint32_t r = lane; r < nd.len; r += 32) ebuf[r] = ld_stream(rows_in + nd.base + r);
       __syncwarp();
     }
     uint64_t chunk = items[lane < count ? lane : 0u];  // items j..j+31 of the group, one per lane
@@ -1351,8 +1374,9 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
         scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu), mine);
         hist_unstage<KIND>(d, hw, occ, mine);
       } else {
-        build_hist<KIND>(d, nd.base, nd.len, rows_in, column(d, f), hw);
+        build_hist<KIND, false>(d, nd.base, nd.len, rows_in, column(d, f), hw);
         scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu));
+        __syncwarp();
         hist_clear<KIND>(d, hw);
         __syncwarp();
       }

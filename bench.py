@@ -370,7 +370,8 @@ def run_gpu(args):
     params = w.params()
     nc = params.pop("n_classes")
     precision = args.precision
-    S = boruta.Session(X, y, N=w.N, n_classes=nc, precision=precision, job=rank, **params)
+    S = boruta.Session(X, y, N=w.N, n_classes=nc, precision=precision, job=rank, autotune=int(args.autotune),
+                       **params)
     R = Stepper(S, w.max_iter)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2, written between steps
     stream = torch.cuda.current_stream()
@@ -378,6 +379,7 @@ def run_gpu(args):
         R.ready()
         R.step()
     R.reset()
+    tuning = S.tuning() if args.autotune else None
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -482,6 +484,9 @@ def run_gpu(args):
                         "levels": [[int(c), round(float(a), 3), round(float(h), 3)] for c, a, h in levels[:-1]],
                         "levels_note": "last timed step, per depth: nodes, split-stage ms, histogram-kernel ms"},
         "permut_walks": walks,
+        "tile_autotune": ({"candidates": [{"group_work": gw, "band_mib": bb >> 20, "launch_per_band": bl,
+                                           "iteration_ms": round(ms, 2)} for gw, bb, bl, ms in tuning[0]],
+                           "chosen": tuning[1]} if tuning else None),
         "other_form": other,
         "batch": batch,
         "e2e": {"value": e2e_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_iters,
@@ -657,6 +662,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5, help="iterations of the end-to-end boruta_fit")
     ap.add_argument("--batch-steps", type=int, default=3, help="iterations of the batched leg")
     ap.add_argument("--trees", type=int, default=None, help="fewer trees (profiling captures only)")
+    ap.add_argument("--autotune", action="store_true", help="time the histogram tile shapes on the first step")
     ap.add_argument("--jobs", type=int, default=64, help="batch workload: number of jobs")
     ap.add_argument("--graph", action="store_true", help="batch workload: replay each job's iterations as CUDA graphs")
     args = ap.parse_args()

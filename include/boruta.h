@@ -84,11 +84,14 @@ typedef struct {
   int forest_rows; /* permut_form = 1: rows per block of the (row, column) accumulators (0 = as
                       many as fit in about 1 GiB, the default); results are identical */
   int autotune;    /* 1: the first step of a session (of every job of a batch) times its
-                      iteration once per histogram tile shape -- column bytes per feature band
-                      (12, 24, 48 MiB) x row-feature work per group of a larger node (4096, 8192,
-                      16384) -- restoring the state after each, and keeps the fastest; results
-                      are identical for every shape (boruta_session_tuning reports the
-                      timings).  0 (default): 24 MiB, 8192. */
+                      iteration once per histogram tile shape, restoring the state after each,
+                      and keeps the fastest: column bytes per feature band (12, 24, 48 MiB) x
+                      one histogram launch per chunk of nodes or per band, at 8192 row-feature
+                      work per group of a larger node; then 4096 and 16384 at the best of
+                      those.  Results are identical for every shape (boruta_session_tuning
+                      reports the timings).  0 (default): 24 MiB, one launch per chunk, 8192. */
+  int band_launch; /* without autotune: 1 = one histogram launch per feature band (all warps on
+                      one band at a time), 0 = one per chunk of nodes (default); same results */
 } boruta_opts;
 
 /* Host-side, caller-allocated outputs. */
@@ -247,11 +250,12 @@ int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* lau
 
 /* The autotuner's measurements (opts->autotune = 1): *n_tried candidates, of
  * which the first `capacity` are written (any pointer may be NULL): the
- * row-feature work per group, the column bytes per band, and the
- * milliseconds of the timed iteration; *chosen is the index kept (-1 before
- * the first step or without autotune). */
+ * row-feature work per group, the column bytes per band, 1 for one
+ * histogram launch per band (0: per chunk), and the milliseconds of the
+ * timed iteration; *chosen is the index kept (-1 before the first step or
+ * without autotune). */
 int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried, uint32_t* group_work,
-                          int64_t* band_bytes, double* ms, int32_t* chosen);
+                          int64_t* band_bytes, int32_t* band_launch, double* ms, int32_t* chosen);
 
 /* Timing of the last step's importance stage (Alg. 2 normalisation, or the
  * Alg. 3 tree walks and their reduction), from CUDA events on the session's

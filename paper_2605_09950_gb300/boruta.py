@@ -46,7 +46,7 @@ class Opts(ct.Structure):
                 ("n_classes", ct.c_int), ("kl_eps", ct.c_double), ("stream", ct.c_void_p),
                 ("job", ct.c_uint32), ("host_inputs", ct.c_int), ("graph", ct.c_int), ("split_path", ct.c_int),
                 ("chunk_nodes", ct.c_int), ("permut_form", ct.c_int), ("forest_rows", ct.c_int),
-                ("autotune", ct.c_int)]
+                ("autotune", ct.c_int), ("band_launch", ct.c_int)]
 
 
 class Job(ct.Structure):
@@ -94,7 +94,8 @@ def lib():
                                                   ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                                   ct.POINTER(ct.c_double)]
         L.boruta_session_importance_stats.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
-        L.boruta_session_tuning.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_int32), vp, vp, vp, ct.POINTER(ct.c_int32)]
+        L.boruta_session_tuning.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_int32), vp, vp, vp, vp,
+                                            ct.POINTER(ct.c_int32)]
         L.boruta_session_destroy.argtypes = [vp]
         L.boruta_session_destroy.restype = None
         L.boruta_batch_create.argtypes = [ct.c_int, vp, vp, ct.POINTER(ct.c_void_p)]
@@ -135,12 +136,13 @@ def _stream():
 
 def make_opts(stat=0, precision=0, tie_break=0, n_classes=0, kl_eps=1e-7, job=0, host_inputs=0,
               graph=0, split_path=0, chunk_nodes=0, permut_form=0, forest_rows=0, autotune=0,
-              stream=None) -> Opts:
+              band_launch=0, stream=None) -> Opts:
     o = Opts()
     lib().boruta_default_opts(ct.byref(o))
     o.stat, o.precision, o.tie_break, o.n_classes = stat, precision, tie_break, n_classes
     o.kl_eps, o.job, o.host_inputs, o.graph, o.split_path = kl_eps, job, host_inputs, graph, split_path
     o.chunk_nodes, o.permut_form, o.forest_rows, o.autotune = chunk_nodes, permut_form, forest_rows, autotune
+    o.band_launch = band_launch
     o.stream = stream if stream is not None else (None if host_inputs else _stream())
     return o
 
@@ -308,15 +310,17 @@ class Session:
                     split_bytes=sb.value)
 
     def tuning(self):
-        """The autotuner's candidates: list of (group work, band bytes, ms) and the index kept."""
+        """The autotuner's candidates: list of (group work, band bytes, per-band launch, ms)
+        and the index kept."""
         n, ch = ct.c_int32(), ct.c_int32()
         gw = np.zeros(16, np.uint32)
         bb = np.zeros(16, np.int64)
+        bl = np.zeros(16, np.int32)
         ms = np.zeros(16)
-        _check(lib().boruta_session_tuning(self._h, 16, ct.byref(n), gw.ctypes.data, bb.ctypes.data, ms.ctypes.data,
-                                           ct.byref(ch)))
+        _check(lib().boruta_session_tuning(self._h, 16, ct.byref(n), gw.ctypes.data, bb.ctypes.data, bl.ctypes.data,
+                                           ms.ctypes.data, ct.byref(ch)))
         k = min(n.value, 16)
-        return [(int(gw[i]), int(bb[i]), float(ms[i])) for i in range(k)], ch.value
+        return [(int(gw[i]), int(bb[i]), int(bl[i]), float(ms[i])) for i in range(k)], ch.value
 
     def importance_stats(self):
         ms, visits = ct.c_double(), ct.c_double()

@@ -64,6 +64,7 @@ struct boruta_session {
   bool autotune = false, tuned = false;
   std::vector<uint32_t> tune_gw;
   std::vector<int64_t> tune_bb;
+  std::vector<int32_t> tune_bl;
   std::vector<double> tune_ms;
   int tune_chosen = -1;
   int pending_t = 0;  // iteration enqueued and not yet finished
@@ -161,6 +162,7 @@ static int check_args(const uint8_t* X, int64_t ld, const void* y, int64_t N, in
   if (o->permut_form < 0 || o->permut_form > 1) return fail(BORUTA_EINVAL, "opts: permut_form takes 0 or 1");
   if (o->forest_rows < 0) return fail(BORUTA_EINVAL, "opts: forest_rows must not be negative");
   if (o->autotune < 0 || o->autotune > 1) return fail(BORUTA_EINVAL, "opts: autotune takes 0 or 1");
+  if (o->band_launch < 0 || o->band_launch > 1) return fail(BORUTA_EINVAL, "opts: band_launch takes 0 or 1");
   if (o->permut_form == 1 && !(task & BORUTA_PERMUT))
     return fail(BORUTA_EINVAL, "opts: permut_form = 1 is a form of Alg. 3 (task needs BORUTA_PERMUT)");
   if (o->precision < 0 || o->precision > 1 || o->tie_break < 0 || o->tie_break > 1 || o->stat < 0 ||
@@ -206,6 +208,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   d.max_iter = max_iter;
   d.precision = o->precision;
   d.group_work = kGroupWork;
+  d.band_launch = o->band_launch;
   d.permut_form = d.permut ? o->permut_form : 0;
   d.tie_break = o->tie_break;
   d.stat = o->stat;
@@ -550,13 +553,18 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
 static int step_finish(boruta_session* s, int32_t* undecided);
 
 // Histogram tile shape by measurement: the next iteration is run once per
-// candidate (column bytes per feature band x row-feature work per group),
-// timed with CUDA events, and the state is restored after each run; the
-// fastest candidate is kept.  The candidates give identical results (the
-// shape decides only which warp does which part of the same sums).
+// candidate, timed with CUDA events, and the state is restored after each
+// run; the fastest candidate is kept.  First the column bytes per feature
+// band (12, 24, 48 MiB) x one histogram launch per chunk or per band, at
+// 8192 row-feature work per group; then 4096 and 16384 at the best of
+// those.  The candidates give identical results (the shape decides only
+// which warp does which part of the same sums, and when).
 static int tune_tiles(boruta_session* s) {
-  static const uint32_t kGw[] = {4096u, 8192u, 16384u};
-  static const int64_t kBb[] = {int64_t{12} << 20, int64_t{24} << 20, int64_t{48} << 20};
+  struct Shape {
+    uint32_t gw;
+    int64_t bb;
+    int32_t bl;
+  };
   const int64_t p = s->p, T = s->max_iter;
   std::vector<int8_t> dec(p);
   std::vector<int32_t> hits(p);
@@ -572,34 +580,52 @@ static int tune_tiles(boruta_session* s) {
   s->tune_ms.clear();
   const bool graph = s->graph;
   s->graph = false;
-  for (uint32_t gw : kGw)
-    for (int64_t bb : kBb) {
-      s->d.group_work = gw;
-      s->band_bytes = bb;
-      CK(cudaEventRecord(e[0], s->st));
-      rc = enqueue_iteration(s, t0 + 1, s->st);
-      if (!rc) {
-        s->pending_t = t0 + 1;
-        CK(cudaEventRecord(e[1], s->st));
-        rc = step_finish(s, nullptr);
-      }
-      float ms = 0.f;
-      if (!rc) CK(cudaEventElapsedTime(&ms, e[0], e[1]));
-      if (!rc) rc = boruta_session_write(s, dec.data(), hits.data(), hist.data(), smax.data(), t0);
-      if (rc) break;
-      s->tune_gw.push_back(gw);
-      s->tune_bb.push_back(bb);
+  s->tune_bl.clear();
+  auto run = [&](const Shape& sh) -> int {
+    s->d.group_work = sh.gw;
+    s->band_bytes = sh.bb;
+    s->d.band_launch = sh.bl;
+    CK(cudaEventRecord(e[0], s->st));
+    int r = enqueue_iteration(s, t0 + 1, s->st);
+    if (!r) {
+      s->pending_t = t0 + 1;
+      CK(cudaEventRecord(e[1], s->st));
+      r = step_finish(s, nullptr);
+    }
+    float ms = 0.f;
+    if (!r) CK(cudaEventElapsedTime(&ms, e[0], e[1]));
+    if (!r) r = boruta_session_write(s, dec.data(), hits.data(), hist.data(), smax.data(), t0);
+    if (!r) {
+      s->tune_gw.push_back(sh.gw);
+      s->tune_bb.push_back(sh.bb);
+      s->tune_bl.push_back(sh.bl);
       s->tune_ms.push_back(ms);
     }
+    return r;
+  };
+  auto best_index = [&]() {
+    size_t b = 0;
+    for (size_t i = 1; i < s->tune_ms.size(); ++i)
+      if (s->tune_ms[i] < s->tune_ms[b]) b = i;
+    return b;
+  };
+  for (int64_t bb : {int64_t{12} << 20, int64_t{24} << 20, int64_t{48} << 20})
+    for (int32_t bl : {0, 1})
+      if (!rc) rc = run(Shape{kGroupWork, bb, bl});
+  if (!rc) {
+    const size_t b = best_index();
+    const Shape at{0u, s->tune_bb[b], s->tune_bl[b]};
+    for (uint32_t gw : {4096u, 16384u})
+      if (!rc) rc = run(Shape{gw, at.bb, at.bl});
+  }
   cudaEventDestroy(e[0]);
   cudaEventDestroy(e[1]);
   s->graph = graph;
   if (rc) return rc;
-  size_t best = 0;
-  for (size_t i = 1; i < s->tune_ms.size(); ++i)
-    if (s->tune_ms[i] < s->tune_ms[best]) best = i;
+  const size_t best = best_index();
   s->d.group_work = s->tune_gw[best];
   s->band_bytes = s->tune_bb[best];
+  s->d.band_launch = s->tune_bl[best];
   s->tune_chosen = static_cast<int>(best);
   return 0;
 }
@@ -767,7 +793,7 @@ int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* lau
 }
 
 int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried, uint32_t* group_work,
-                          int64_t* band_bytes, double* ms, int32_t* chosen) {
+                          int64_t* band_bytes, int32_t* band_launch, double* ms, int32_t* chosen) {
   if (!s) return fail(BORUTA_EINVAL, "session is NULL");
   const int n = static_cast<int>(s->tune_ms.size());
   if (n_tried) *n_tried = n;
@@ -775,6 +801,7 @@ int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried,
   for (int i = 0; i < n && i < capacity; ++i) {
     if (group_work) group_work[i] = s->tune_gw[i];
     if (band_bytes) band_bytes[i] = s->tune_bb[i];
+    if (band_launch) band_launch[i] = s->tune_bl[i];
     if (ms) ms[i] = s->tune_ms[i];
   }
   return 0;

@@ -63,6 +63,7 @@ struct Dev {
   uint64_t item_cap;
   int32_t band_w, nbands;        // columns per band (0: grouped path only), bands
   uint32_t group_work;           // row x feature work per group of a larger node (tile shape)
+  int32_t band_launch;           // 1: one histogram launch per feature band, 0: one per chunk
   uint32_t chunk0, chunk_cap;    // band path: first larger node of the chunk, nodes per chunk
   // ---- importance and Boruta state
   long long* acc;                // [M][p_aug][kCsaLimbs] exact per-tree accumulators (carry-save)

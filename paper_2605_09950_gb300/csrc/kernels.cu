@@ -520,14 +520,6 @@ __device__ float loss32(const Dev& d, uint32_t q, uint32_t q2) {
   return kl;
 }
 
-// The loss of one re-walk that reached leaf q2 instead of q, added to the
-// exact accumulator of (tree, feature f).  Not inlined: the walk loop stays
-// small enough for the instruction cache.
-__device__ __noinline__ void add_loss(const Dev& d, int tau, uint32_t f, uint32_t q, uint32_t q2) {
-  const double L = d.precision == 0 ? loss64(d, q, q2) : static_cast<double>(loss32(d, q, q2));
-  if (!csa_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + f) * kCsaLimbs, L)) atomicOr(&d.status[0], kErrAcc);
-}
-
 // One thread per (tree, OOB row): walk the row's path; for each distinct
 // feature f on it, re-walk from f's first node with x_f replaced by
 // X[pi(i)][f] (all later f nodes use the swapped value too).  Features off
@@ -640,11 +632,17 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
           if (!busy) break;
         }
         // the losses, in a loop that is not unrolled: one copy of the loss code
+        uint32_t leaf[kWalks];
+#pragma unroll
+        for (int u = 0; u < kWalks; ++u) leaf[u] = wk[u];
 #pragma unroll 1
         for (int u = 0; u < kWalks; ++u) {
-          const uint32_t q2 = wk[u];
+          const uint32_t q2 = leaf[u];
           if (w0 + u >= nw || q2 == q) continue;
-          add_loss(d, tau, wfx[w0 + u] >> 8, q, q2);
+          const uint32_t f = wfx[w0 + u] >> 8;
+          const double L = d.precision == 0 ? loss64(d, q, q2) : static_cast<double>(loss32(d, q, q2));
+          if (!csa_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + f) * kCsaLimbs, L))
+            atomicOr(&d.status[0], kErrAcc);
         }
       }
     }

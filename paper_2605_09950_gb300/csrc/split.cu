@@ -1080,10 +1080,11 @@ __device__ void scan_pack(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* 
 // hist_unstage); the bins that receive rows are marked in occ.
 template <int KIND>
 __device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const uint32_t* ebuf,
-                                            const uint32_t (&b)[kRegRows / 32], uint32_t* hw, uint32_t* occ) {
+                                            const uint32_t (&b)[kRegRows / 32], uint32_t* hw, uint32_t* occ,
+                                            bool mark) {
   const int lane = threadIdx.x & 31;
   if (regs4(d, KIND)) {
-    if (lane == 0) occ[0] = (1u << d.B) - 1u;  // regs4_store writes bins 0..B-1
+    if (lane == 0 && mark) occ[0] = (1u << d.B) - 1u;  // regs4_store writes bins 0..B-1
     uint32_t c0[4] = {0u, 0u, 0u, 0u}, c1[4] = {0u, 0u, 0u, 0u};
     long long sy[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -1103,7 +1104,7 @@ __device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const ui
       if (r < len) {
         const uint32_t e = ebuf[r];
         atomicAdd(&hw[b[q] * d.C + ent_y(e) + (b[q] >> 3)], ent_w<0>(e));
-        atomicOr(&occ[b[q] >> 5], 1u << (b[q] & 31u));
+        if (mark) atomicOr(&occ[b[q] >> 5], 1u << (b[q] & 31u));
       }
     }
   } else {
@@ -1118,7 +1119,7 @@ __device__ __forceinline__ void hist_staged(const Dev& d, uint32_t len, const ui
         const long long yq = d.yreg[e >> 8];
         atomicAdd(&hn[b[q] + (b[q] >> 3)], w);
         atomicAdd(&hs[b[q] + (b[q] >> 3)], static_cast<unsigned long long>(static_cast<long long>(w) * yq));
-        atomicOr(&occ[b[q] >> 5], 1u << (b[q] & 31u));
+        if (mark) atomicOr(&occ[b[q] >> 5], 1u << (b[q] & 31u));
       }
     }
   }
@@ -1321,8 +1322,10 @@ __global__ void __launch_bounds__(256) k_plan_scatter(Dev d, int level) {
 }
 
 // one warp per group: each feature's exact best candidate, packed
+// band < 0: every group of the chunk; else only the groups of that band
+// (one launch per band keeps the warps, and the L2, on one band at a time).
 template <int KIND, int CM>
-__global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band(Dev d, int level) {
+__global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band(Dev d, int level, int band) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
@@ -1335,9 +1338,14 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t* rows_in = d.rows[level & 1];
-  const uint32_t total = d.band_cnt[kMaxBands];
+  // after k_plan_scatter band_cnt[b] is the end of band b's groups
+  const uint32_t g0 = band <= 0 ? 0u : d.band_cnt[band - 1];
+  const uint32_t g1 = band < 0 ? d.band_cnt[kMaxBands] : d.band_cnt[band];
+  // staged nodes: the scan reads only the occupied bins when the histogram
+  // is large (it is then mostly empty); small histograms are read whole
+  const bool sparse = d.B * (KIND ? 3 : ncls<CM>(d)) >= 512;
   unsigned long long bytes = 0;
-  for (uint32_t g = gwarp; g < total; g += nwarps) {
+  for (uint32_t g = g0 + gwarp; g < g1; g += nwarps) {
     const uint64_t gr = d.items_s[g];
     const uint32_t rank = static_cast<uint32_t>(gr >> 28);
     const uint32_t first = static_cast<uint32_t>(gr >> 14) & 0x3FFFu;
@@ -1369,10 +1377,17 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
         if (j + 1 < count)
           gather_staged(column(d, static_cast<uint32_t>(__shfl_sync(kFull, chunk, (j + 1) & 31) & 0x3FFFFFu)),
                         nd.len, ebuf, bn);
-        hist_staged<KIND>(d, nd.len, ebuf, b, hw, occ);
-        const uint32_t mine = lane_occ(d, occ);
-        scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu), mine);
-        hist_unstage<KIND>(d, hw, occ, mine);
+        hist_staged<KIND>(d, nd.len, ebuf, b, hw, occ, sparse);
+        if (sparse) {
+          const uint32_t mine = lane_occ(d, occ);
+          scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu), mine);
+          hist_unstage<KIND>(d, hw, occ, mine);
+        } else {
+          scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu));
+          __syncwarp();
+          hist_clear<KIND>(d, hw);
+          __syncwarp();
+        }
       } else {
         build_hist<KIND, false>(d, nd.base, nd.len, rows_in, column(d, f), hw);
         scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu));
@@ -1546,7 +1561,10 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, uint6
     // the histogram kernel of the level (with several chunks the window also
     // holds the later chunks' plan and finalize kernels)
     if (c == 0 && hist_start) cudaEventRecord(hist_start, st);
-    k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(dc, level);
+    if (d.band_launch)
+      for (int b = 0; b < d.nbands; ++b) k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(dc, level, b);
+    else
+      k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(dc, level, -1);
     if (c + 1 == nchunks && hist_end) cudaEventRecord(hist_end, st);
     k_finalize_band<KIND, CM><<<grid_small, 256, 0, st>>>(dc, level);
   }

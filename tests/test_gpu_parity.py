@@ -276,10 +276,11 @@ def test_graph_replay_matches_stream_launches(importance):
 
 @pytest.mark.parametrize("importance", [synth.TREEIMP, synth.PERMUT])
 def test_autotuned_tiles_give_the_same_run(importance):
-    """opts.autotune = 1: the first step times the nine histogram tile shapes
-    (band bytes x group work) on iteration 1, restoring the state after each,
-    and keeps the fastest; the run is the same, bit for bit, as with the
-    default shape, and the batched form with autotune equals it too."""
+    """opts.autotune = 1: the first step times eight histogram tile shapes
+    (band bytes x launch per chunk or per band, then group work) on
+    iteration 1, restoring the state after each, and keeps the fastest; the
+    run is the same, bit for bit, as with the default shape, and the batched
+    form with autotune equals it too."""
     import torch
 
     from paper_2605_09950_gb300 import boruta
@@ -296,8 +297,8 @@ def test_autotuned_tiles_give_the_same_run(importance):
     for key in ("decision", "hits", "imp_history", "shadow_max", "iterations"):
         np.testing.assert_array_equal(ra[key], rb[key], err_msg=key)
     tried, chosen = B.tuning()
-    assert len(tried) == 9 and 0 <= chosen < 9 and all(ms > 0 for _, _, ms in tried)
-    assert {gw for gw, _, _ in tried} == {4096, 8192, 16384}
+    assert len(tried) == 8 and 0 <= chosen < 8 and all(ms > 0 for _, _, _, ms in tried)
+    assert {gw for gw, _, _, _ in tried} == {4096, 8192, 16384} and {bl for _, _, bl, _ in tried} == {0, 1}
     assert A.tuning() == ([], -1)
     params = w.params()
     job = dict(X=torch.from_numpy(w.X).cuda(), y=torch.from_numpy(w.y).cuda(), N=w.N, **params)
@@ -405,9 +406,12 @@ def test_band_path_in_many_chunks(case):
     S, _, _, imp = check_iteration(w, chunk_nodes=3)
     ref = session(w)
     ref.step()
+    per_band = session(w, chunk_nodes=3, band_launch=1)  # one histogram launch per band
+    per_band.step()
     for what, dt in ((boruta.DUMP_NODES, boruta.NODE_DTYPE), (boruta.DUMP_IMP, np.float64),
                      (boruta.DUMP_STAT, np.float64)):
         np.testing.assert_array_equal(S.dump(what, dt), ref.dump(what, dt))
+        np.testing.assert_array_equal(per_band.dump(what, dt), ref.dump(what, dt))
     levels = S.dump(boruta.DUMP_LEVELS, np.float64).reshape(-1, 3)
     assert levels[:, 0].max() > 3 * 3  # some level held more than three chunks of nodes
 

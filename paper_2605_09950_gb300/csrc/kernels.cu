@@ -631,16 +631,13 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
           }
           if (!busy) break;
         }
-        // the losses, in a loop that is not unrolled: one copy of the loss code
-        uint32_t leaf[kWalks];
+        // the losses, unrolled: the leaves' statistics of the kWalks re-walks
+        // load together
 #pragma unroll
-        for (int u = 0; u < kWalks; ++u) leaf[u] = wk[u];
-#pragma unroll 1
         for (int u = 0; u < kWalks; ++u) {
-          const uint32_t q2 = leaf[u];
-          if (w0 + u >= nw || q2 == q) continue;
+          if (w0 + u >= nw || wk[u] == q) continue;
           const uint32_t f = wfx[w0 + u] >> 8;
-          const double L = d.precision == 0 ? loss64(d, q, q2) : static_cast<double>(loss32(d, q, q2));
+          const double L = d.precision == 0 ? loss64(d, q, wk[u]) : static_cast<double>(loss32(d, q, wk[u]));
           if (!csa_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + f) * kCsaLimbs, L))
             atomicOr(&d.status[0], kErrAcc);
         }

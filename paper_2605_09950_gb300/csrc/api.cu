@@ -355,6 +355,8 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
       cap, static_cast<size_t>(n_trees) * std::min<uint64_t>(1ull << max_depth, static_cast<uint64_t>(N)));
   if ((rc = s->alloc(&d.small, level_cap))) return rc;
   if ((rc = s->alloc(&d.nsmall, max_depth + 2))) return rc;
+  if ((rc = s->alloc(&d.ntiny, max_depth + 2))) return rc;
+  d.small_cap = static_cast<uint32_t>(level_cap);
   uint8_t* cand = nullptr;
   if ((rc = s->alloc(&cand, big_cap * kItemsPerNode * cand_bytes(split_variant(d.kind, d.C))))) return rc;
   d.cand = cand;
@@ -493,6 +495,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   CK(cudaMemsetAsync(d.acc, 0, static_cast<size_t>(d.M) * p_aug * kCsaLimbs * sizeof(long long), st));
   CK(cudaMemsetAsync(d.work, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.nsmall, 0, (d.D + 2) * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(d.ntiny, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.lvl_cnt, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.counters, 0, 4 * sizeof(unsigned long long), st));
 

@@ -52,7 +52,9 @@ struct Dev {
   uint32_t* chunk;               // [kScanBlocks] per-block split counts
   uint32_t* big;                 // [big_cap] this level's active nodes with > 32 rows
   uint32_t* small;               // [level_cap] this level's active nodes with <= 32 rows
-  uint32_t* nsmall;              // [D + 2] per level: number of nodes in `small`
+  uint32_t* nsmall;              // [D + 2] per level: number of 17..32-row nodes at the start of `small`
+  uint32_t* ntiny;               // [D + 2] per level: number of <= 16-row nodes at the end of `small`
+  uint32_t small_cap;            // entries of `small`
   void* ninfo;                   // [big_cap] node totals of `big`, by rank
   void* cand;                    // [big_cap * kItemsPerNode] best candidate per grouped item
   uint64_t* items_u;             // [item_cap] (node rank, slot, feature) per item; each node's

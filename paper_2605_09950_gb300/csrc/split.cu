@@ -397,21 +397,94 @@ struct SmallPlanes {
   unsigned y[CM];
 };
 
-// Best split of one feature for a node of <= 32 rows, one row per lane.
-// Classification: the lanes whose bin is <= this lane's bin come from eight
-// ballots over the bin bits (most significant first), and the left class
-// counts from population counts against the weight and class bit planes.
-// Regression: the left sums are accumulated over the rows by shuffles.
-// Updates the node's exact best (best) and best float score so far (bestf).
-template <int KIND, int CM>
+// A small node's rows sit one per lane in a segment of SEG lanes: the whole
+// warp (SEG = 32, nodes of 17..32 rows) or a half warp (SEG = 16: two nodes
+// of <= 16 rows per warp, one in each half).  Segment helpers: the lanes'
+// mask, and reductions that stay inside the segment.
+template <int SEG>
+__device__ __forceinline__ unsigned seg_mask() {
+  return SEG == 32 ? kFull : (0xFFFFu << ((threadIdx.x & 31) & 16));
+}
+
+template <int SEG>
+__device__ __forceinline__ float seg_max_f(float v) {
+#pragma unroll
+  for (int off = SEG / 2; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, off));
+  return v;
+}
+
+template <int SEG>
+__device__ __forceinline__ uint32_t seg_sum_u32(uint32_t v) {
+  if (SEG == 32) return __reduce_add_sync(kFull, v);
+#pragma unroll
+  for (int off = SEG / 2; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+template <int SEG>
+__device__ __forceinline__ long long seg_sum_i64(long long v) {
+#pragma unroll
+  for (int off = SEG / 2; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+// best of the segment's lane candidates flagged valid (all lanes take part;
+// each segment walks its own candidates, as many rounds as the busier one)
+template <int KIND, int CM, int SEG>
+__device__ void seg_select(const Cand<CM>& mine, Cand<CM>& out) {
+  if (SEG == 32) {
+    warp_select<KIND, CM>(mine, out);
+    return;
+  }
+  unsigned m = __ballot_sync(kFull, mine.valid) & seg_mask<SEG>();
+  const int rounds = __reduce_max_sync(kFull, static_cast<unsigned>(__popc(m)));
+  out.valid = false;
+  for (int r = 0; r < rounds; ++r) {
+    const bool have = m != 0u;
+    const int l = have ? __ffs(m) - 1 : static_cast<int>(threadIdx.x & 31);
+    if (have) m &= m - 1;
+    Cand<CM> c;
+    c.num.w[0] = __shfl_sync(kFull, mine.num.w[0], l);
+    c.num.w[1] = __shfl_sync(kFull, mine.num.w[1], l);
+    c.num.w[2] = __shfl_sync(kFull, mine.num.w[2], l);
+    c.den = __shfl_sync(kFull, mine.den, l);
+    c.key = __shfl_sync(kFull, mine.key, l);
+    c.nL = __shfl_sync(kFull, mine.nL, l);
+    c.feat = __shfl_sync(kFull, mine.feat, l);
+    c.bin = __shfl_sync(kFull, mine.bin, l);
+    if (KIND == 1) {
+      c.SL = __shfl_sync(kFull, mine.SL, l);
+#pragma unroll
+      for (int k = 0; k < CM; ++k) c.cL[k] = 0u;
+    } else {
+      c.SL = 0;
+#pragma unroll
+      for (int k = 0; k < CM; ++k) c.cL[k] = __shfl_sync(kFull, mine.cL[k], l);
+    }
+    c.valid = have;
+    if (better(c, out)) out = c;
+  }
+}
+
+// Best split of one feature for a node of <= SEG rows, one row per lane of
+// its segment.  Classification: the lanes whose bin is <= this lane's bin
+// come from eight ballots over the bin bits (most significant first), and
+// the left class counts from population counts against the weight and class
+// bit planes.  Regression: the left sums are accumulated over the rows by
+// shuffles (rows up to lenmax, the longest node of the warp; lanes past a
+// node's rows carry weight 0).  Updates the node's exact best (best) and
+// best float score so far (bestf).  Every lane runs every warp-wide step:
+// a segment with nothing to contribute goes on with no candidate.
+template <int KIND, int CM, int SEG>
 __device__ void small_feature(const NodeInfo<CM>& nd, int C, int B, bool v, uint32_t b, uint32_t w, uint32_t y,
                               long long yv, const SmallPlanes<CM>& pl, int feat, uint32_t tkey, float& bestf,
-                              Cand<CM>& best) {
+                              Cand<CM>& best, uint32_t lenmax) {
+  const unsigned sm = seg_mask<SEG>();
   if (KIND == 1 && B <= 4) {
     // Regression on a column of at most 4 bins: the left sums of each of
-    // the <= 3 thresholds come from warp reductions, the same on every lane.
-    // A threshold whose bin holds no row repeats the partition of a lower
-    // one and loses the tie to it.
+    // the <= 3 thresholds come from segment reductions, the same on every
+    // lane of the segment.  A threshold whose bin holds no row repeats the
+    // partition of a lower one and loses the tie to it.
     float sf[3];
     uint32_t nLt[3];
     long long SLt[3];
@@ -423,10 +496,8 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, int B, bool v, uint
       SLt[t] = 0;
       if (t >= B - 1) break;  // uniform
       const bool in = v && b <= static_cast<uint32_t>(t);
-      const uint32_t nl = __reduce_add_sync(kFull, in ? w : 0u);
-      long long sl = in ? static_cast<long long>(w) * yv : 0ll;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) sl += __shfl_xor_sync(kFull, sl, off);
+      const uint32_t nl = seg_sum_u32<SEG>(in ? w : 0u);
+      const long long sl = seg_sum_i64<SEG>(in ? static_cast<long long>(w) * yv : 0ll);
       nLt[t] = nl;
       SLt[t] = sl;
       if (nl > 0u && nl < nd.n) {
@@ -434,7 +505,7 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, int B, bool v, uint
         mx = fmaxf(mx, sf[t]);
       }
     }
-    if (mx < 0.0f || mx < screen(bestf)) return;
+    if (mx < 0.0f || mx < screen(bestf)) return;  // no warp-wide step follows
     const float thr = screen(fmaxf(mx, bestf));
     bestf = fmaxf(mx, bestf);
 #pragma unroll
@@ -456,7 +527,7 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, int B, bool v, uint
   long long SL = 0;
   unsigned same;
   if (KIND == 0) {
-    unsigned lt = 0u, eq = pl.valid;
+    unsigned lt = 0u, eq = pl.valid & sm;
 #pragma unroll
     for (int t = 7; t >= 0; --t) {
       const unsigned bt = __ballot_sync(kFull, (b >> t) & 1u);
@@ -477,29 +548,33 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, int B, bool v, uint
       }
     same = v ? eq : 0u;
   } else {
-    for (int j = 0; j < static_cast<int>(nd.len); ++j) {
-      const uint32_t bj = __shfl_sync(kFull, b, j), wj = __shfl_sync(kFull, w, j);
-      const long long yj = __shfl_sync(kFull, yv, j);
-      if (bj <= b) {
+    const int base = static_cast<int>(threadIdx.x & 31) & ~(SEG - 1);
+    for (int j = 0; j < static_cast<int>(lenmax); ++j) {
+      const uint32_t bj = __shfl_sync(kFull, b, base + j), wj = __shfl_sync(kFull, w, base + j);
+      const long long yj = __shfl_sync(kFull, yv, base + j);
+      if (bj <= b) {  // rows past the node's own carry weight 0
         nL += wj;
         SL += static_cast<long long>(wj) * yj;
       }
     }
-    same = __match_any_sync(kFull, v ? b : 0xFFFFFFFFu);
+    same = __match_any_sync(kFull, v ? b : 0xFFFFFFFFu) & sm;
   }
   // lanes holding the same bin propose the same partition: the lowest one speaks
-  const bool ok = v && nL < nd.n && (__ffs(same) - 1) == (threadIdx.x & 31);
+  const bool ok = v && nL < nd.n && (__ffs(same) - 1) == static_cast<int>(threadIdx.x & 31);
   float sf = -1.0f;
   if (ok) sf = KIND == 1 ? score_reg_f(SL, nd.SP, nL, nd.n) : score_class_f<CM>(cl, nd.cp, C, nL, nd.n);
-  const float mx = warp_max_f(sf);
+  const float mx = seg_max_f<SEG>(sf);
   // a feature whose best float score is below the window of the node's best
   // so far cannot hold the node's exact best
-  if (mx < 0.0f || mx < screen(bestf)) return;
-  const float thr = screen(fmaxf(mx, bestf));
-  bestf = fmaxf(mx, bestf);
+  const bool take = !(mx < 0.0f || mx < screen(bestf));
+  float thr = 0.0f;
+  if (take) {
+    thr = screen(fmaxf(mx, bestf));
+    bestf = fmaxf(mx, bestf);
+  }
   Cand<CM> mine;
   mine.valid = false;
-  if (ok && sf >= thr) {
+  if (take && ok && sf >= thr) {
     if (KIND == 1)
       make_reg<CM>(mine, SL, nd.SP, nL, nd.n);
     else
@@ -509,12 +584,13 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, int B, bool v, uint
     mine.key = (tkey << 8) | b;
   }
   Cand<CM> c;
-  warp_select<KIND, CM>(mine, c);
-  if (better(c, best)) best = c;
+  seg_select<KIND, CM, SEG>(mine, c);
+  if (take && better(c, best)) best = c;
 }
 
 // One thread per node of the level: leaves are marked, active nodes are
-// listed as small (<= 32 rows) or larger (warp-aggregated appends).
+// listed as tiny (<= 16 rows, from the end of `small`), small (17..32 rows,
+// from its start) or larger (warp-aggregated appends).
 template <int KIND, int CM>
 __global__ void __launch_bounds__(256) k_classify(Dev d, int level) {
   const int lane = threadIdx.x & 31;
@@ -522,103 +598,139 @@ __global__ void __launch_bounds__(256) k_classify(Dev d, int level) {
   for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < lcount;
        base += gridDim.x * blockDim.x) {
     const uint32_t idx = base + lane;
-    int cls = 0;  // 0 none, 1 small, 2 larger
+    int cls = 0;  // 0 none, 1 small, 2 larger, 3 tiny
     uint32_t k = 0;
     if (idx < lcount) {
       k = loff + idx;
       NodeInfo<CM> nd;
       if (load_node<KIND, CM>(d, k, level, nd))
-        cls = nd.len > 32u ? 2 : 1;
+        cls = nd.len > 32u ? 2 : (nd.len > 16u ? 1 : 3);
       else
         d.nd_split[k] = kLeaf;
     }
-    const unsigned ms = __ballot_sync(kFull, cls == 1), mb = __ballot_sync(kFull, cls == 2);
-    uint32_t s0 = 0, b0 = 0;
+    const unsigned ms = __ballot_sync(kFull, cls == 1), mb = __ballot_sync(kFull, cls == 2),
+                   mt = __ballot_sync(kFull, cls == 3);
+    uint32_t s0 = 0, b0 = 0, t0 = 0;
     if (lane == 0) {
       if (ms) s0 = atomicAdd(&d.nsmall[level], static_cast<uint32_t>(__popc(ms)));
       if (mb) b0 = atomicAdd(&d.work[level], static_cast<uint32_t>(__popc(mb)));
+      if (mt) t0 = atomicAdd(&d.ntiny[level], static_cast<uint32_t>(__popc(mt)));
     }
     s0 = __shfl_sync(kFull, s0, 0);
     b0 = __shfl_sync(kFull, b0, 0);
+    t0 = __shfl_sync(kFull, t0, 0);
     if (cls == 1) d.small[s0 + __popc(ms & lanemask_lt())] = k;
     if (cls == 2) d.big[b0 + __popc(mb & lanemask_lt())] = k;
+    if (cls == 3) d.small[d.small_cap - 1u - (t0 + __popc(mt & lanemask_lt()))] = k;
   }
 }
 
-template <int KIND, int CM>
+constexpr uint32_t kNoNode = 0xFFFFFFFFu;
+
+// The split of the small node k of this lane's segment (kNoNode: none; its
+// lanes still take part in every warp-wide step), its record and partition.
+template <int KIND, int CM, int SEG>
+__device__ void small_node(const Dev& d, int level, uint32_t k, uint8_t* sbin, unsigned long long& bytes) {
+  const int lane = threadIdx.x & 31;
+  const int hl = lane & (SEG - 1);
+  const uint32_t* rows_in = d.rows[level & 1];
+  uint32_t* rows_out = d.rows[(level & 1) ^ 1];
+  const int C = ncls<CM>(d);
+  const bool has = k != kNoNode;
+  NodeInfo<CM> nd;
+  nd.base = 0;
+  nd.len = 0u;
+  nd.n = 0u;
+  nd.SP = 0;
+#pragma unroll
+  for (int c = 0; c < CM; ++c) nd.cp[c] = 0u;
+  Perm P;
+  if (has) {
+    load_node<KIND, CM>(d, k, level, nd);
+    node_perm(d, k, P);
+  }
+  const bool v = hl < static_cast<int>(nd.len);
+  const uint32_t e = v ? rows_in[nd.base + hl] : 0u;
+  const uint32_t row = e >> 8, w = v ? ent_w<KIND>(e) : 0u;
+  const uint32_t y = KIND == 0 ? ent_y(e) : 0u;
+  const long long yv = (KIND == 1 && v) ? d.yreg[row] : 0ll;
+  SmallPlanes<CM> pl;
+  pl.valid = __ballot_sync(kFull, v);
+#pragma unroll
+  for (int t = 0; t < 5; ++t) pl.w[t] = __ballot_sync(kFull, (w >> t) & 1u);
+#pragma unroll
+  for (int c = 0; c < CM; ++c) pl.y[c] = __ballot_sync(kFull, v && y == static_cast<uint32_t>(c));
+  const uint32_t lenmax = SEG == 32 ? nd.len : __reduce_max_sync(kFull, nd.len);
+  Cand<CM> best;
+  best.valid = false;
+  float bestf = -1.0f;
+  for (int r0 = 0; r0 < d.mtry; r0 += SEG) {
+    const int ns = min(SEG, d.mtry - r0);
+    const uint32_t myf = (has && hl < ns) ? perm_apply(P, static_cast<uint32_t>(r0 + hl)) : 0u;
+    for (int j0 = 0; j0 < ns; j0 += kSmallAhead) {
+      // the row's bins of the next kSmallAhead features, all loads in
+      // flight at once (the shuffles run on all lanes, outside the per-lane
+      // conditions), parked in the warp's shared memory
+      uint32_t bv[kSmallAhead];
+#pragma unroll
+      for (int u = 0; u < kSmallAhead; ++u) {
+        const uint32_t fu = __shfl_sync(kFull, myf, min(j0 + u, ns - 1), SEG);
+        bv[u] = (v && j0 + u < ns) ? column(d, fu)[row] : 0u;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kSmallAhead; ++u) sbin[u * 32 + lane] = static_cast<uint8_t>(bv[u]);
+      __syncwarp();
+      const int nu = min(kSmallAhead, ns - j0);
+      for (int u = 0; u < nu; ++u) {
+        const uint32_t f = __shfl_sync(kFull, myf, j0 + u, SEG);
+        const uint32_t tkey = d.tie_break == 1 ? static_cast<uint32_t>(r0 + j0 + u) : f;
+        small_feature<KIND, CM, SEG>(nd, C, d.B, v, sbin[u * 32 + lane], w, y, yv, pl, static_cast<int>(f), tkey,
+                                     bestf, best, lenmax);
+      }
+    }
+  }
+  uint32_t sp = kLeaf;
+  if (has && hl == 0) sp = commit_split<KIND, CM>(d, k, best, nd);
+  sp = __shfl_sync(kFull, sp, 0, SEG);
+  if (has && hl == 0) bytes += static_cast<unsigned long long>(nd.len) * (d.mtry + 4ull + (KIND ? 8ull : 0ull));
+  // stable partition: left rows in order, then right rows in order
+  const bool split = has && sp != kLeaf;
+  const uint32_t bs = (v && split) ? column(d, sp >> 8)[row] : 0u;
+  const bool gl = v && split && bs <= (sp & 255u), gr = v && split && !gl;
+  const unsigned sm = seg_mask<SEG>();
+  const unsigned bl = __ballot_sync(kFull, gl) & sm, br = __ballot_sync(kFull, gr) & sm;
+  const uint32_t nl = __popc(bl);
+  if (gl) rows_out[nd.base + __popc(bl & lanemask_lt())] = e;
+  if (gr) rows_out[nd.base + nl + __popc(br & lanemask_lt())] = e;
+  if (split && hl == 0) {
+    d.nd_lrows[k] = nl;
+    bytes += static_cast<unsigned long long>(nd.len) * 5ull;
+  }
+}
+
+// SEG = 16: one warp per pair of tiny nodes (a half warp each);
+// SEG = 32: one warp per small node.
+template <int KIND, int CM, int SEG>
 __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, int level) {
   __shared__ uint8_t sbins[8][kSmallAhead * 32];
   const int lane = threadIdx.x & 31;
   uint8_t* sbin = sbins[threadIdx.x >> 5];
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t* rows_in = d.rows[level & 1];
-  uint32_t* rows_out = d.rows[(level & 1) ^ 1];
-  const uint32_t ns_nodes = d.nsmall[level];
-  const int C = ncls<CM>(d);
   unsigned long long bytes = 0;
-  for (uint32_t idx = gwarp; idx < ns_nodes; idx += nwarps) {
-    const uint32_t k = d.small[idx];
-    NodeInfo<CM> nd;
-    load_node<KIND, CM>(d, k, level, nd);
-    Perm P;
-    node_perm(d, k, P);
-    const bool v = lane < static_cast<int>(nd.len);
-    const uint32_t e = v ? rows_in[nd.base + lane] : 0u;
-    const uint32_t row = e >> 8, w = v ? ent_w<KIND>(e) : 0u;
-    const uint32_t y = KIND == 0 ? ent_y(e) : 0u;
-    const long long yv = (KIND == 1 && v) ? d.yreg[row] : 0ll;
-    SmallPlanes<CM> pl;
-    pl.valid = __ballot_sync(kFull, v);
-#pragma unroll
-    for (int t = 0; t < 5; ++t) pl.w[t] = __ballot_sync(kFull, (w >> t) & 1u);
-#pragma unroll
-    for (int c = 0; c < CM; ++c) pl.y[c] = __ballot_sync(kFull, v && y == static_cast<uint32_t>(c));
-    Cand<CM> best;
-    best.valid = false;
-    float bestf = -1.0f;
-    for (int r0 = 0; r0 < d.mtry; r0 += 32) {
-      const int ns = min(32, d.mtry - r0);
-      const uint32_t myf = lane < ns ? perm_apply(P, static_cast<uint32_t>(r0 + lane)) : 0u;
-      for (int j0 = 0; j0 < ns; j0 += kSmallAhead) {
-        // the row's bins of the next kSmallAhead features, all loads in
-        // flight at once (the shuffles run on all lanes, outside the per-lane
-        // conditions), parked in the warp's shared memory
-        uint32_t bv[kSmallAhead];
-#pragma unroll
-        for (int u = 0; u < kSmallAhead; ++u) {
-          const uint32_t fu = __shfl_sync(kFull, myf, min(j0 + u, ns - 1));
-          bv[u] = (v && j0 + u < ns) ? column(d, fu)[row] : 0u;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int u = 0; u < kSmallAhead; ++u) sbin[u * 32 + lane] = static_cast<uint8_t>(bv[u]);
-        __syncwarp();
-        const int nu = min(kSmallAhead, ns - j0);
-        for (int u = 0; u < nu; ++u) {
-          const uint32_t f = __shfl_sync(kFull, myf, j0 + u);
-          const uint32_t tkey = d.tie_break == 1 ? static_cast<uint32_t>(r0 + j0 + u) : f;
-          small_feature<KIND, CM>(nd, C, d.B, v, sbin[u * 32 + lane], w, y, yv, pl, static_cast<int>(f), tkey, bestf,
-                                  best);
-        }
-      }
+  if (SEG == 16) {
+    const uint32_t nt = d.ntiny[level], npairs = (nt + 1u) / 2u;
+    for (uint32_t idx = gwarp; idx < npairs; idx += nwarps) {
+      const uint32_t t = 2u * idx + static_cast<uint32_t>(lane >> 4);
+      const uint32_t k = t < nt ? d.small[d.small_cap - 1u - t] : kNoNode;
+      small_node<KIND, CM, SEG>(d, level, k, sbin, bytes);
     }
-    uint32_t sp = 0;
-    if (lane == 0) sp = commit_split<KIND, CM>(d, k, best, nd);
-    sp = __shfl_sync(kFull, sp, 0);
-    bytes += static_cast<unsigned long long>(nd.len) * (d.mtry + 4ull + (KIND ? 8ull : 0ull));
-    if (sp == kLeaf) continue;
-    // stable partition: left rows in order, then right rows in order
-    const uint32_t bs = v ? column(d, sp >> 8)[row] : 0u;
-    const bool gl = v && bs <= (sp & 255u), gr = v && !gl;
-    const unsigned bl = __ballot_sync(kFull, gl), br = __ballot_sync(kFull, gr);
-    const uint32_t nl = __popc(bl);
-    if (gl) rows_out[nd.base + __popc(bl & lanemask_lt())] = e;
-    if (gr) rows_out[nd.base + nl + __popc(br & lanemask_lt())] = e;
-    if (lane == 0) d.nd_lrows[k] = nl;
-    bytes += static_cast<unsigned long long>(nd.len) * 5ull;
+  } else {
+    const uint32_t ns_nodes = d.nsmall[level];
+    for (uint32_t idx = gwarp; idx < ns_nodes; idx += nwarps) small_node<KIND, CM, SEG>(d, level, d.small[idx], sbin, bytes);
   }
-  if (lane == 0 && bytes) atomicAdd(&d.counters[0], bytes);
+  if (bytes) atomicAdd(&d.counters[0], bytes);
 }
 
 // ============================================================ larger nodes
@@ -1545,7 +1657,8 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, uint6
   // small nodes on st2, concurrently with the larger-node kernels on st
   cudaEventRecord(fork, st);
   cudaStreamWaitEvent(st2, fork, 0);
-  k_split_small<KIND, CM><<<grid_small, 256, 0, st2>>>(d, level);
+  k_split_small<KIND, CM, 16><<<grid_small, 256, 0, st2>>>(d, level);
+  k_split_small<KIND, CM, 32><<<grid_small, 256, 0, st2>>>(d, level);
   cudaEventRecord(join, st2);
   // band path: the larger nodes in chunks of chunk_cap (at most big_bound
   // nodes exist; chunks past the level's count return at once)
@@ -1624,7 +1737,7 @@ void split_kernel_ptrs(int variant, const void** ptrs, int* n) {
 
 const void* small_kernel_ptr(int variant) {
   return with_variant(variant, [](auto kind, auto cm) {
-    return reinterpret_cast<const void*>(&k_split_small<decltype(kind)::value, decltype(cm)::value>);
+    return reinterpret_cast<const void*>(&k_split_small<decltype(kind)::value, decltype(cm)::value, 32>);
   });
 }
 

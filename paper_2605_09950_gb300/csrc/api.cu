@@ -417,7 +417,8 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   s->tree_grid = std::min(n_trees, 8 * s->sms);
   s->permut_grid = 16 * s->sms;
   int walk_per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, permut_kernel_ptr(), 128, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, permut_kernel_ptr(d.precision), 128,
+                                                   permut_smem_bytes(max_depth)));
   s->walk_grid = std::max(1, walk_per_sm) * s->sms;
   s->ev.resize(2 * (max_depth + 1));
   for (auto& e : s->ev) CK(cudaEventCreate(&e));

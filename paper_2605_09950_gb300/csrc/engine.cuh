@@ -127,7 +127,8 @@ void launch_children(const Dev& d, int level, cudaStream_t st);
 void launch_treeimp(const Dev& d, int grid, cudaStream_t st);
 void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st);
 void launch_forest_permut(const Dev& d, int grid, cudaStream_t st);
-const void* permut_kernel_ptr();  // for its occupancy
+const void* permut_kernel_ptr(int precision);  // for its occupancy
+size_t permut_smem_bytes(int D);                // its dynamic shared memory per block (128 threads)
 void launch_stats_decide(const Dev& d, cudaStream_t st);
 // Warp-private histogram layout.  A lane scans 8 consecutive bins, so one
 // padding slot follows every 8 bins: lane l's block then starts at a bank

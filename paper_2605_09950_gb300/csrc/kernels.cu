@@ -524,22 +524,48 @@ __device__ float loss32(const Dev& d, uint32_t q, uint32_t q2) {
 // feature f on it, re-walk from f's first node with x_f replaced by
 // X[pi(i)][f] (all later f nodes use the swapped value too).  Features off
 // the path leave the leaf unchanged and add exactly 0.
+// The re-walks of a warp's 32 rows are pooled in the warp's shared memory
+// and dealt round-robin to its lanes, kWalks at a time per lane, so that a
+// lane whose row has few re-walks takes over those of a row with many.
 // Work items are (tree, chunk of 128 OOB rows), dealt round-robin to a grid
 // of exactly the blocks the GPU holds at once, so no partial last wave.
+// PREC: the precision form (0 = FP64 terms, 1 = FP32 terms), a template
+// argument so that each instantiation holds one loss routine.
+__host__ __device__ inline size_t permut_smem_per_warp(int D) {
+  // walk pool: start node and feature << 8 | swapped bin (32 * D each), the
+  // owning lane (32 * D bytes), then each lane's row and base leaf
+  return static_cast<size_t>(32 * D) * 9 + 64 * 4;
+}
+
+template <int PREC>
 __global__ void __launch_bounds__(128) k_permut(Dev d) {
+  extern __shared__ __align__(16) uint32_t pool[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cap = 32 * d.D;
+  uint32_t* q_node = pool + warp * (permut_smem_per_warp(d.D) / 4);
+  uint32_t* q_fx = q_node + cap;
+  uint32_t* o_row = q_fx + cap;
+  uint32_t* o_leaf = o_row + 32;
+  uint8_t* q_own = reinterpret_cast<uint8_t*>(o_leaf + 32);
   const uint32_t chunks = (static_cast<uint32_t>(d.N) + 127u) / 128u;
   const uint64_t items = static_cast<uint64_t>(d.M) * chunks;
   unsigned long long visits = 0;  // nodes whose test a walk applied (the base path and the re-walks)
+  constexpr int kWalks = BORUTA_PERMUT_WALKS;
   for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
     const int tau = static_cast<int>(item / chunks);
     const uint32_t noob = d.oob_cnt[tau];
+    const uint32_t r0 = static_cast<uint32_t>(item - static_cast<uint64_t>(tau) * chunks) * 128u;
+    if (r0 >= noob) continue;  // block-uniform
     const uint32_t* oob = d.oob + static_cast<int64_t>(tau) * d.N;
-    const uint32_t r = static_cast<uint32_t>(item - static_cast<uint64_t>(tau) * chunks) * 128u + threadIdx.x;
-    if (r >= noob) continue;
-    {
-      const uint32_t i = oob[r];
+    const uint32_t r = r0 + threadIdx.x;
+    uint32_t i = 0u, q = 0u;
+    int nw = 0;
+    uint32_t wnode[kMaxDepth];  // node at which the swapped row leaves the path
+    uint32_t wfx[kMaxDepth];    // feature << 8 | swapped bin
+    if (r < noob) {
+      i = oob[r];
       const uint32_t pi = d.piv[i];
-      const uint8_t* xi = d.Xrow + static_cast<int64_t>(i) * d.ldP;  // the row's bins, row-major
+      const uint8_t* xi = d.Xrow + static_cast<int64_t>(i) * d.ldP;    // the row's bins, row-major
       const uint8_t* xpi = d.Xrow + static_cast<int64_t>(pi) * d.ldP;  // the flush_index row's bins
       // the row's path: node, split word, and the row's own bin at each node;
       // the children's words are loaded with the bin (one round trip a level)
@@ -561,7 +587,7 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
         s = right ? n1.x : n0.x;
         c = right ? n1.y : n0.y;
       }
-      const uint32_t q = k;
+      q = k;
       visits += static_cast<unsigned long long>(depth);
       // the permuted row's bins of every feature on the path, loaded together
       uint8_t xq[kMaxDepth];
@@ -569,9 +595,6 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
       // the re-walks: for each distinct feature f on the path whose swapped
       // value sends the row the other way at some node testing f, the walk
       // restarts at that node's other child
-      uint32_t wstart[kMaxDepth];  // node at which the swapped row leaves the path
-      uint32_t wfx[kMaxDepth];     // feature << 8 | swapped bin
-      int nw = 0;
       for (int a = 0; a < depth; ++a) {
         const uint32_t f = pw[a] >> 8;
         bool seen = false;
@@ -586,63 +609,79 @@ __global__ void __launch_bounds__(128) k_permut(Dev d) {
         for (; b < depth; ++b)
           if ((pw[b] >> 8) == f && ((xp > (pw[b] & 255u)) != (px[b] > (pw[b] & 255u)))) break;
         if (b == depth) continue;
-        wstart[nw] = (b << 1) | ((xp > (pw[b] & 255u)) ? 1u : 0u);
+        wnode[nw] = d.nd_sc[path[b]].y + ((xp > (pw[b] & 255u)) ? 1u : 0u);
         wfx[nw] = (f << 8) | xp;
         ++nw;
       }
-      // kWalks re-walks advance together (independent loads in flight)
-      constexpr int kWalks = BORUTA_PERMUT_WALKS;
-      for (int w0 = 0; w0 < nw; w0 += kWalks) {
-        uint32_t wk[kWalks], ws[kWalks], wc[kWalks];
+    }
+    // pool the warp's re-walks (nw <= depth <= D per lane)
+    const uint32_t off = warp_excl_scan_u32(static_cast<uint32_t>(nw), lane);
+    const uint32_t W = __shfl_sync(kFull, off + static_cast<uint32_t>(nw), 31);
+    for (int j = 0; j < nw; ++j) {
+      q_node[off + j] = wnode[j];
+      q_fx[off + j] = wfx[j];
+      q_own[off + j] = static_cast<uint8_t>(lane);
+    }
+    o_row[lane] = i;
+    o_leaf[lane] = q;
+    __syncwarp();
+    // kWalks re-walks per lane advance together (independent loads in flight)
+    for (uint32_t e0 = 0; e0 < W; e0 += 32u * kWalks) {
+      uint32_t wk[kWalks], ws[kWalks], wc[kWalks], fx[kWalks];
+      const uint8_t* xr[kWalks];
 #pragma unroll
-        for (int u = 0; u < kWalks; ++u) {
-          wk[u] = 0u;
-          ws[u] = kLeaf;
-          wc[u] = 0u;
-          if (w0 + u < nw) {
-            // the other child of the node where the swapped value turns
-            const uint32_t at = wstart[w0 + u];
-            wk[u] = d.nd_sc[path[at >> 1]].y + (at & 1u);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kWalks; ++u)
-          if (w0 + u < nw) {
-            const uint2 n = d.nd_sc[wk[u]];
-            ws[u] = n.x;
-            wc[u] = n.y;
-          }
-        for (int guard = 0; guard <= kMaxDepth; ++guard) {  // trees are at most kMaxDepth deep
-          bool busy = false;
-#pragma unroll
-          for (int u = 0; u < kWalks; ++u) {
-            if (ws[u] == kLeaf) continue;
-            busy = true;
-            ++visits;
-            const uint32_t fx = wfx[w0 + u];
-            const uint32_t g = ws[u] >> 8;
-            const uint8_t x = (g == (fx >> 8)) ? static_cast<uint8_t>(fx & 255u) : xi[g];
-            const uint32_t c = wc[u];
-            const uint2 n0 = d.nd_sc[c], n1 = d.nd_sc[c + 1];
-            const bool right = x > (ws[u] & 255u);
-            wk[u] = c + (right ? 1u : 0u);
-            ws[u] = right ? n1.x : n0.x;
-            wc[u] = right ? n1.y : n0.y;
-          }
-          if (!busy) break;
-        }
-        // the losses, unrolled: the leaves' statistics of the kWalks re-walks
-        // load together
-#pragma unroll
-        for (int u = 0; u < kWalks; ++u) {
-          if (w0 + u >= nw || wk[u] == q) continue;
-          const uint32_t f = wfx[w0 + u] >> 8;
-          const double L = d.precision == 0 ? loss64(d, q, wk[u]) : static_cast<double>(loss32(d, q, wk[u]));
-          if (!csa_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + f) * kCsaLimbs, L))
-            atomicOr(&d.status[0], kErrAcc);
+      for (int u = 0; u < kWalks; ++u) {
+        const uint32_t e = e0 + static_cast<uint32_t>(u) * 32u + lane;
+        wk[u] = 0u;
+        ws[u] = kLeaf;
+        wc[u] = 0u;
+        fx[u] = 0u;
+        xr[u] = d.Xrow;
+        if (e < W) {
+          wk[u] = q_node[e];
+          fx[u] = q_fx[e];
+          xr[u] = d.Xrow + static_cast<int64_t>(o_row[q_own[e]]) * d.ldP;
         }
       }
+#pragma unroll
+      for (int u = 0; u < kWalks; ++u)
+        if (e0 + static_cast<uint32_t>(u) * 32u + lane < W) {
+          const uint2 n = d.nd_sc[wk[u]];
+          ws[u] = n.x;
+          wc[u] = n.y;
+        }
+      for (int guard = 0; guard <= kMaxDepth; ++guard) {  // trees are at most kMaxDepth deep
+        bool busy = false;
+#pragma unroll
+        for (int u = 0; u < kWalks; ++u) {
+          if (ws[u] == kLeaf) continue;
+          busy = true;
+          ++visits;
+          const uint32_t g = ws[u] >> 8;
+          const uint8_t x = (g == (fx[u] >> 8)) ? static_cast<uint8_t>(fx[u] & 255u) : xr[u][g];
+          const uint32_t c = wc[u];
+          const uint2 n0 = d.nd_sc[c], n1 = d.nd_sc[c + 1];
+          const bool right = x > (ws[u] & 255u);
+          wk[u] = c + (right ? 1u : 0u);
+          ws[u] = right ? n1.x : n0.x;
+          wc[u] = right ? n1.y : n0.y;
+        }
+        if (!busy) break;
+      }
+      // the losses, unrolled: the leaves' statistics of the kWalks re-walks
+      // load together
+#pragma unroll
+      for (int u = 0; u < kWalks; ++u) {
+        const uint32_t e = e0 + static_cast<uint32_t>(u) * 32u + lane;
+        if (e >= W) continue;
+        const uint32_t qo = o_leaf[q_own[e]];
+        if (wk[u] == qo) continue;
+        const double L = PREC == 0 ? loss64(d, qo, wk[u]) : static_cast<double>(loss32(d, qo, wk[u]));
+        if (!csa_add(d.acc + (static_cast<int64_t>(tau) * d.p_aug + (fx[u] >> 8)) * kCsaLimbs, L))
+          atomicOr(&d.status[0], kErrAcc);
+      }
     }
+    __syncwarp();  // the pool is refilled by the next item
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) visits += __shfl_xor_sync(kFull, visits, off);
@@ -672,11 +711,19 @@ void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
   k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
   k_transpose_rows<<<grid, 256, 0, st>>>(d);
   k_pack_nodes<<<grid, 256, 0, st>>>(d);
-  k_permut<<<walk_grid, 128, 0, st>>>(d);
+  const size_t smem = 4 * permut_smem_per_warp(d.D);
+  if (d.precision == 0)
+    k_permut<0><<<walk_grid, 128, smem, st>>>(d);
+  else
+    k_permut<1><<<walk_grid, 128, smem, st>>>(d);
   k_permut_final<<<grid, 256, 0, st>>>(d);
 }
 
-const void* permut_kernel_ptr() { return reinterpret_cast<const void*>(&k_permut); }
+size_t permut_smem_bytes(int D) { return 4 * permut_smem_per_warp(D); }
+
+const void* permut_kernel_ptr(int precision) {
+  return precision == 0 ? reinterpret_cast<const void*>(&k_permut<0>) : reinterpret_cast<const void*>(&k_permut<1>);
+}
 
 // ============================================================ Alg. 3 as printed: all rows, forest
 // The model is the whole forest: a row's prediction is the mean over the M

@@ -85,10 +85,10 @@ typedef struct {
                       many as fit in about 1 GiB, the default); results are identical */
   int autotune;    /* 1: the first step of a session (of every job of a batch) times its
                       iteration once per histogram tile shape, restoring the state after each,
-                      and keeps the fastest: column bytes per feature band (12, 24, 48 MiB) x
-                      one histogram launch per chunk of nodes or per band, at 8192 row-feature
-                      work per group of a larger node; then 4096 and 16384 at the best of
-                      those.  Results are identical for every shape (boruta_session_tuning
+                      and keeps the fastest: column bytes per feature band (12, 24, 48, 96
+                      MiB) x one histogram launch per chunk of nodes or per band, and a single
+                      band (no band order), at 8192 row-feature work per group of a larger
+                      node; then 4096 and 16384 at the best of those.  Results are identical for every shape (boruta_session_tuning
                       reports the timings).  0 (default): 24 MiB, one launch per chunk, 8192. */
   int band_launch; /* without autotune: 1 = one histogram launch per feature band (all warps on
                       one band at a time), 0 = one per chunk of nodes (default); same results */

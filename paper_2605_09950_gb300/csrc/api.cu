@@ -487,6 +487,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   if (s->split_path == 0 && d.chunk_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
     int64_t w = std::max<int64_t>(1, s->band_bytes / d.ldN);
     w = std::max<int64_t>(w, (p_aug + kMaxBands - 1) / kMaxBands);
+    w = std::min<int64_t>(w, p_aug);  // one band at most holds every column
     d.band_w = static_cast<int32_t>(w);
     d.nbands = static_cast<int32_t>((p_aug + w - 1) / w);
   }
@@ -559,9 +560,9 @@ static int step_finish(boruta_session* s, int32_t* undecided);
 // Histogram tile shape by measurement: the next iteration is run once per
 // candidate, timed with CUDA events, and the state is restored after each
 // run; the fastest candidate is kept.  First the column bytes per feature
-// band (12, 24, 48 MiB) x one histogram launch per chunk or per band, at
-// 8192 row-feature work per group; then 4096 and 16384 at the best of
-// those.  The candidates give identical results (the shape decides only
+// band (12, 24, 48, 96 MiB) x one histogram launch per chunk or per band,
+// and a single band (no band order), at 8192 row-feature work per group;
+// then 4096 and 16384 at the best of those.  The candidates give identical results (the shape decides only
 // which warp does which part of the same sums, and when).
 static int tune_tiles(boruta_session* s) {
   struct Shape {
@@ -613,9 +614,9 @@ static int tune_tiles(boruta_session* s) {
       if (s->tune_ms[i] < s->tune_ms[b]) b = i;
     return b;
   };
-  for (int64_t bb : {int64_t{12} << 20, int64_t{24} << 20, int64_t{48} << 20})
+  for (int64_t bb : {int64_t{12} << 20, int64_t{24} << 20, int64_t{48} << 20, int64_t{96} << 20, int64_t{1} << 40})
     for (int32_t bl : {0, 1})
-      if (!rc) rc = run(Shape{kGroupWork, bb, bl});
+      if (!rc && !(bl == 1 && bb > (int64_t{96} << 20))) rc = run(Shape{kGroupWork, bb, bl});
   if (!rc) {
     const size_t b = best_index();
     const Shape at{0u, s->tune_bb[b], s->tune_bl[b]};

@@ -276,8 +276,9 @@ def test_graph_replay_matches_stream_launches(importance):
 
 @pytest.mark.parametrize("importance", [synth.TREEIMP, synth.PERMUT])
 def test_autotuned_tiles_give_the_same_run(importance):
-    """opts.autotune = 1: the first step times eight histogram tile shapes
-    (band bytes x launch per chunk or per band, then group work) on
+    """opts.autotune = 1: the first step times eleven histogram tile shapes
+    (band bytes x launch per chunk or per band, a single band, then group
+    work) on
     iteration 1, restoring the state after each, and keeps the fastest; the
     run is the same, bit for bit, as with the default shape, and the batched
     form with autotune equals it too."""
@@ -297,7 +298,7 @@ def test_autotuned_tiles_give_the_same_run(importance):
     for key in ("decision", "hits", "imp_history", "shadow_max", "iterations"):
         np.testing.assert_array_equal(ra[key], rb[key], err_msg=key)
     tried, chosen = B.tuning()
-    assert len(tried) == 8 and 0 <= chosen < 8 and all(ms > 0 for _, _, _, ms in tried)
+    assert len(tried) == 11 and 0 <= chosen < 11 and all(ms > 0 for _, _, _, ms in tried)
     assert {gw for gw, _, _, _ in tried} == {4096, 8192, 16384} and {bl for _, _, bl, _ in tried} == {0, 1}
     assert A.tuning() == ([], -1)
     params = w.params()

@@ -89,7 +89,7 @@ typedef struct {
                       MiB) x one histogram launch per chunk of nodes or per band, and a single
                       band (no band order), at 8192 row-feature work per group of a larger
                       node; then 4096 and 16384 at the best of those.  Results are identical for every shape (boruta_session_tuning
-                      reports the timings).  0 (default): 24 MiB, one launch per chunk, 8192. */
+                      reports the timings).  0 (default): 48 MiB, one launch per chunk, 8192. */
   int band_launch; /* without autotune: 1 = one histogram launch per feature band (all warps on
                       one band at a time), 0 = one per chunk of nodes (default); same results */
 } boruta_opts;

@@ -91,7 +91,7 @@ constexpr int kScanBlocks = 512;
 constexpr int kSplitThreads = 256;
 constexpr int kItemsPerNode = 16;  // work items (groups of draw slots) per larger node
 constexpr int kMaxBands = 256;     // feature bands of the band-sorted path
-constexpr int64_t kBandBytes = 24ll << 20;  // column bytes per band (kept in L2 while in use)
+constexpr int64_t kBandBytes = 48ll << 20;  // default column bytes per feature band
 constexpr uint64_t kMaxItems = 128ull << 20;  // plan buffer capacity (items)
 constexpr int kMaxIterations = 126;          // max_iter limit (exact binomial tails in 128 bits)
 #ifndef BORUTA_STAGED_ROWS

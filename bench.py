@@ -370,8 +370,11 @@ def run_gpu(args):
     params = w.params()
     nc = params.pop("n_classes")
     precision = args.precision
+    t_setup = time.perf_counter()
     S = boruta.Session(X, y, N=w.N, n_classes=nc, precision=precision, job=rank, autotune=int(args.autotune),
                        **params)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
     R = Stepper(S, w.max_iter)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2, written between steps
     stream = torch.cuda.current_stream()
@@ -380,6 +383,7 @@ def run_gpu(args):
         R.step()
     R.reset()
     tuning = S.tuning() if args.autotune else None
+    tuning_levels = S.tuning_levels() if args.autotune else None
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -397,6 +401,7 @@ def run_gpu(args):
         ks["visits"] += im["node_visits"]
         if R.t == k_other and not snap:
             snap.update(S.read())
+            snap["imp"] = S.dump(boruta.DUMP_IMP, np.float64)
 
     step_ms = timed_steps(R, args.steps, stream, flush, collect)
     levels = S.dump(boruta.DUMP_LEVELS, np.float64).reshape(-1, 3)
@@ -414,13 +419,19 @@ def run_gpu(args):
         R2.reset()
         ms2 = timed_steps(R2, k_other, stream, flush)
         res2 = S2.read()
+        imp2 = S2.dump(boruta.DUMP_IMP, np.float64)
         S2.close()
         del S2
         same = bool(snap) and bool((res2["decision"] == snap["decision"]).all() and
                                    (res2["hits"] == snap["hits"]).all())
+        rel = None
+        if snap and snap["imp"].shape == imp2.shape:  # the two forms' importance rows at iteration k
+            den = np.maximum(np.abs(snap["imp"]), np.abs(imp2))
+            rel = float(np.max(np.where(den > 0, np.abs(snap["imp"] - imp2) / np.where(den > 0, den, 1), 0.0)))
         other = {"precision": "fp64 terms" if precision else "fp32 terms", "steps": k_other,
                  "value": k_other / (sum(ms2) / 1000.0), "unit": UNIT,
-                 "identical_hits_and_decisions_after_steps": same}
+                 "identical_hits_and_decisions_after_steps": same,
+                 "max_rel_importance_difference_at_last_step": rel}
 
     # end to end through the C ABI with host buffers (upload + iterations + readback)
     k_e2e = max(1, min(args.steps, args.e2e_steps, w.max_iter))
@@ -470,7 +481,7 @@ def run_gpu(args):
                    "tie_break": "lowest (feature, bin)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "512 MiB buffer written before each timed step; inputs and per-step working set > L2",
-                   "input_generation_s": round(gen_s, 1)},
+                   "input_generation_s": round(gen_s, 1), "session_setup_s": round(setup_s, 2)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
                      "traffic_source": prof["profile"] if traffic else None,
@@ -484,9 +495,15 @@ def run_gpu(args):
                         "levels": [[int(c), round(float(a), 3), round(float(h), 3)] for c, a, h in levels[:-1]],
                         "levels_note": "last timed step, per depth: nodes, split-stage ms, histogram-kernel ms"},
         "permut_walks": walks,
-        "tile_autotune": ({"candidates": [{"group_work": gw, "band_mib": bb >> 20, "launch_per_band": bl,
+        "tile_autotune": ({"candidates": [{"group_work": gw, "band_mib": bb >> 20 if bb >= 0 else "per level",
+                                           "launch_per_band": bl if bl >= 0 else "per level",
                                            "iteration_ms": round(ms, 2)} for gw, bb, bl, ms in tuning[0]],
-                           "chosen": tuning[1]} if tuning else None),
+                           "chosen": tuning[1],
+                           "per_level": {"band_mib": [b >> 20 for b in tuning_levels[0]],
+                                         "launch_per_band": tuning_levels[1],
+                                         "level_ms_per_candidate": [[round(float(x), 2) for x in row]
+                                                                    for row in tuning_levels[2]]}}
+                          if tuning else None),
         "other_form": other,
         "batch": batch,
         "e2e": {"value": e2e_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_iters,

@@ -85,13 +85,21 @@ typedef struct {
                       many as fit in about 1 GiB, the default); results are identical */
   int autotune;    /* 1: the first step of a session (of every job of a batch) times its
                       iteration once per histogram tile shape, restoring the state after each,
-                      and keeps the fastest: column bytes per feature band (12, 24, 48, 96
-                      MiB) x one histogram launch per chunk of nodes or per band, and a single
-                      band (no band order), at 8192 row-feature work per group of a larger
-                      node; then 4096 and 16384 at the best of those.  Results are identical for every shape (boruta_session_tuning
-                      reports the timings).  0 (default): 48 MiB, one launch per chunk, 8192. */
-  int band_launch; /* without autotune: 1 = one histogram launch per feature band (all warps on
-                      one band at a time), 0 = one per chunk of nodes (default); same results */
+                      and keeps the fastest: column bytes per feature band (12, 24, 48, 96,
+                      192 MiB) x one histogram launch per chunk of nodes or per band, and a
+                      single band (no band order), at 8192 row-feature work per group of a
+                      larger node, each run also timing every tree level; then the per-level
+                      combination (at each level the shape whose level was fastest) at 8192,
+                      4096 and 16384.  Results are identical for every shape
+                      (boruta_session_tuning and boruta_session_tuning_levels report the
+                      timings and the choice).  0 (default): 48 MiB, launches as
+                      band_launch says, 8192. */
+  int band_launch; /* without autotune: 0 (default) = by level: one histogram launch per feature
+                      band (all warps on one band at a time) at the levels where a band holds at
+                      least twice as many (node, band) groups as the GPU runs warps at once
+                      (counted from the level's largest possible node count), else one per
+                      chunk of nodes; 1 = one per band at every level; 2 = one per chunk at
+                      every level.  Same results. */
 } boruta_opts;
 
 /* Host-side, caller-allocated outputs. */
@@ -256,6 +264,18 @@ int boruta_session_kernel_stats(boruta_session* s, double* hist_ms, int32_t* lau
  * without autotune). */
 int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried, uint32_t* group_work,
                           int64_t* band_bytes, int32_t* band_launch, double* ms, int32_t* chosen);
+
+/* Per tree level (max_depth levels, *n_levels; the first `capacity` are
+ * written; any pointer may be NULL): the column bytes per band the session
+ * uses at that level, the launch mode of its last iteration there (1 per
+ * band, 0 per chunk, -1 before the first step), and, when level_ms is given,
+ * the autotuner's split-stage milliseconds of each level in each candidate
+ * run, row-major [n_tried][capacity] (n_tried from boruta_session_tuning;
+ * the caller allocates n_tried * capacity doubles).  In boruta_session_tuning
+ * a candidate with band_bytes = band_launch = -1 is the per-level
+ * combination. */
+int boruta_session_tuning_levels(boruta_session* s, int32_t capacity, int32_t* n_levels, int64_t* band_bytes,
+                                 int32_t* band_launch, double* level_ms);
 
 /* Timing of the last step's importance stage (Alg. 2 normalisation, or the
  * Alg. 3 tree walks and their reduction), from CUDA events on the session's

@@ -28,7 +28,7 @@ EXPORTS = [
     "boruta_batch_read", "boruta_batch_destroy", "boruta_session_create", "boruta_session_step",
     "boruta_session_read", "boruta_session_write", "boruta_session_dump",
     "boruta_session_kernel_stats", "boruta_session_importance_stats", "boruta_session_tuning",
-    "boruta_session_destroy",
+    "boruta_session_tuning_levels", "boruta_session_destroy",
     "boruta_philox", "boruta_perm",
     "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_quantise",
     "boruta_last_error", "boruta_rank", "boruta_select_median", "boruta_fit_seeds",
@@ -96,6 +96,7 @@ def lib():
         L.boruta_session_importance_stats.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.boruta_session_tuning.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_int32), vp, vp, vp, vp,
                                             ct.POINTER(ct.c_int32)]
+        L.boruta_session_tuning_levels.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_int32), vp, vp, vp]
         L.boruta_session_destroy.argtypes = [vp]
         L.boruta_session_destroy.restype = None
         L.boruta_batch_create.argtypes = [ct.c_int, vp, vp, ct.POINTER(ct.c_void_p)]
@@ -311,16 +312,32 @@ class Session:
 
     def tuning(self):
         """The autotuner's candidates: list of (group work, band bytes, per-band launch, ms)
-        and the index kept."""
+        and the index kept; band bytes and launch are -1 for the per-level combination."""
         n, ch = ct.c_int32(), ct.c_int32()
-        gw = np.zeros(16, np.uint32)
-        bb = np.zeros(16, np.int64)
-        bl = np.zeros(16, np.int32)
-        ms = np.zeros(16)
-        _check(lib().boruta_session_tuning(self._h, 16, ct.byref(n), gw.ctypes.data, bb.ctypes.data, bl.ctypes.data,
+        cap = 32
+        gw = np.zeros(cap, np.uint32)
+        bb = np.zeros(cap, np.int64)
+        bl = np.zeros(cap, np.int32)
+        ms = np.zeros(cap)
+        _check(lib().boruta_session_tuning(self._h, cap, ct.byref(n), gw.ctypes.data, bb.ctypes.data, bl.ctypes.data,
                                            ms.ctypes.data, ct.byref(ch)))
-        k = min(n.value, 16)
+        k = min(n.value, cap)
         return [(int(gw[i]), int(bb[i]), int(bl[i]), float(ms[i])) for i in range(k)], ch.value
+
+    def tuning_levels(self):
+        """Per tree level: the band bytes and launch mode in use, and the
+        autotuner's split-stage ms of that level in each candidate run
+        (array [candidates, levels])."""
+        n_tried = len(self.tuning()[0])
+        cap = 64
+        nl = ct.c_int32()
+        bb = np.zeros(cap, np.int64)
+        bl = np.zeros(cap, np.int32)
+        lm = np.zeros((max(n_tried, 1), cap))
+        _check(lib().boruta_session_tuning_levels(self._h, cap, ct.byref(nl), bb.ctypes.data, bl.ctypes.data,
+                                                  lm.ctypes.data))
+        k = min(nl.value, cap)
+        return bb[:k].tolist(), bl[:k].tolist(), lm[:n_tried, :k]
 
     def importance_stats(self):
         ms, visits = ct.c_double(), ct.c_double()

@@ -61,11 +61,20 @@ struct boruta_session {
   // histogram tile shape: column bytes per feature band and row x feature
   // work per group; opts.autotune times the candidates on the first step
   int64_t band_bytes = kBandBytes;
+  // histogram launches: 0 = per feature band at the levels where a band
+  // holds at least twice as many groups as the GPU runs warps at once (else
+  // per chunk), 1 = per band, 2 = per chunk (opts.band_launch)
+  int band_policy = 0;
+  // per tree level (empty: band_bytes and band_policy at every level)
+  std::vector<int64_t> lvl_bb;
+  std::vector<int32_t> lvl_bl;
+  std::vector<int32_t> used_bw, used_bl;  // band width (columns) and launch mode of each level, last iteration
   bool autotune = false, tuned = false;
   std::vector<uint32_t> tune_gw;
-  std::vector<int64_t> tune_bb;
+  std::vector<int64_t> tune_bb;  // -1: the per-level combination
   std::vector<int32_t> tune_bl;
   std::vector<double> tune_ms;
+  std::vector<std::vector<double>> tune_lvl_ms;  // per candidate: split-stage ms of each level
   int tune_chosen = -1;
   int pending_t = 0;  // iteration enqueued and not yet finished
   bool graph = false;                   // iterations replayed through an instantiated CUDA graph
@@ -162,7 +171,7 @@ static int check_args(const uint8_t* X, int64_t ld, const void* y, int64_t N, in
   if (o->permut_form < 0 || o->permut_form > 1) return fail(BORUTA_EINVAL, "opts: permut_form takes 0 or 1");
   if (o->forest_rows < 0) return fail(BORUTA_EINVAL, "opts: forest_rows must not be negative");
   if (o->autotune < 0 || o->autotune > 1) return fail(BORUTA_EINVAL, "opts: autotune takes 0 or 1");
-  if (o->band_launch < 0 || o->band_launch > 1) return fail(BORUTA_EINVAL, "opts: band_launch takes 0 or 1");
+  if (o->band_launch < 0 || o->band_launch > 2) return fail(BORUTA_EINVAL, "opts: band_launch takes 0, 1 or 2");
   if (o->permut_form == 1 && !(task & BORUTA_PERMUT))
     return fail(BORUTA_EINVAL, "opts: permut_form = 1 is a form of Alg. 3 (task needs BORUTA_PERMUT)");
   if (o->precision < 0 || o->precision > 1 || o->tie_break < 0 || o->tie_break > 1 || o->stat < 0 ||
@@ -208,7 +217,8 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   d.max_iter = max_iter;
   d.precision = o->precision;
   d.group_work = kGroupWork;
-  d.band_launch = o->band_launch;
+  s->band_policy = o->band_launch;
+  d.band_launch = 0;
   d.permut_form = d.permut ? o->permut_form : 0;
   d.tie_break = o->tie_break;
   d.stat = o->stat;
@@ -369,6 +379,7 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
     d.item_cap = cap_items;
     if ((rc = s->alloc(&d.items_u, cap_items))) return rc;
     if ((rc = s->alloc(&d.items_s, cap_items))) return rc;
+    if ((rc = s->alloc(&d.items_b, cap_items))) return rc;
     uint8_t* fb = nullptr;
     if ((rc = s->alloc(&fb, cap_items * packed_bytes(split_variant(d.kind, d.C))))) return rc;
     d.fbest = fb;
@@ -484,13 +495,34 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   d.chunk0 = 0;
   d.chunk_cap = static_cast<uint32_t>(std::min<uint64_t>(d.item_cap / static_cast<uint64_t>(d.mtry), 1u << 26));
   if (s->chunk_nodes > 0) d.chunk_cap = std::min<uint32_t>(d.chunk_cap, static_cast<uint32_t>(s->chunk_nodes));
-  if (s->split_path == 0 && d.chunk_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22)) {
-    int64_t w = std::max<int64_t>(1, s->band_bytes / d.ldN);
+  const bool band_ok = s->split_path == 0 && d.chunk_cap > 0 && d.mtry < (1 << 14) && p_aug < (1 << 22);
+  // the band width and launch mode of a level (big: its larger nodes, at
+  // most; level -1: the iteration's defaults)
+  auto set_band = [&](Dev& dl, int level, uint64_t big) {
+    dl.band_w = 0;
+    dl.nbands = 0;
+    dl.band_launch = 0;
+    if (!band_ok) return;
+    const bool per_level = level >= 0 && level < static_cast<int>(s->lvl_bb.size());
+    const int64_t bb = per_level ? s->lvl_bb[level] : s->band_bytes;
+    int64_t w = std::max<int64_t>(1, bb / d.ldN);
     w = std::max<int64_t>(w, (p_aug + kMaxBands - 1) / kMaxBands);
     w = std::min<int64_t>(w, p_aug);  // one band at most holds every column
-    d.band_w = static_cast<int32_t>(w);
-    d.nbands = static_cast<int32_t>((p_aug + w - 1) / w);
-  }
+    dl.band_w = static_cast<int32_t>(w);
+    dl.nbands = static_cast<int32_t>((p_aug + w - 1) / w);
+    if (per_level) {
+      dl.band_launch = s->lvl_bl[level];
+    } else if (s->band_policy == 1) {
+      dl.band_launch = 1;
+    } else if (s->band_policy == 0 && level >= 0) {
+      // all warps on one band at a time pays once a band's groups fill the
+      // GPU twice over; with fewer, the launches of the bands run part-empty
+      const uint64_t groups_per_band = big * static_cast<uint64_t>(d.mtry) / static_cast<uint64_t>(dl.nbands);
+      const uint64_t resident = static_cast<uint64_t>(s->split_grid) * (kSplitThreads / 32);
+      dl.band_launch = groups_per_band >= 2 * resident ? 1 : 0;
+    }
+  };
+  set_band(d, -1, 0);
 
   CK(cudaMemcpyAsync(s->live_d, s->live_pin, p_live * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d.bootcnt, 0, static_cast<size_t>(d.M) * d.N * sizeof(uint32_t), st));
@@ -524,7 +556,15 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
     const int gs = static_cast<int>(std::min<uint64_t>(s->small_grid, (nodes + 7) / 8));
     const int gi = static_cast<int>(std::min<uint64_t>(s->split_grid, std::max<uint64_t>(1, (groups + 7) / 8)));
     if (timed) CK(cudaEventRecord(s->ev[2 * level], st));
-    launch_split(d, level, std::max(gs, 1), gi, big, s->split_smem, st, s->st2, s->fork, s->join,
+    Dev dl = d;
+    set_band(dl, level, big);
+    if (s->used_bw.size() != static_cast<size_t>(d.D)) {
+      s->used_bw.assign(d.D, 0);
+      s->used_bl.assign(d.D, 0);
+    }
+    s->used_bw[level] = dl.band_w;
+    s->used_bl[level] = dl.band_launch;
+    launch_split(dl, level, std::max(gs, 1), gi, big, s->split_smem, st, s->st2, s->fork, s->join,
                  timed ? s->hev[2 * level] : nullptr, timed ? s->hev[2 * level + 1] : nullptr);
     CK_LAUNCH("split kernels");
     if (timed) CK(cudaEventRecord(s->ev[2 * level + 1], st));
@@ -559,15 +599,17 @@ static int step_finish(boruta_session* s, int32_t* undecided);
 
 // Histogram tile shape by measurement: the next iteration is run once per
 // candidate, timed with CUDA events, and the state is restored after each
-// run; the fastest candidate is kept.  First the column bytes per feature
-// band (12, 24, 48, 96 MiB) x one histogram launch per chunk or per band,
-// and a single band (no band order), at 8192 row-feature work per group;
-// then 4096 and 16384 at the best of those.  The candidates give identical results (the shape decides only
-// which warp does which part of the same sums, and when).
+// run.  First the column bytes per feature band (12, 24, 48, 96, 192 MiB) x
+// one histogram launch per chunk or per band, and a single band (no band
+// order), at 8192 row-feature work per group; each run also times every
+// tree level.  Then the per-level combination -- at each level the shape
+// whose level was fastest -- at 8192, 4096 and 16384 work per group.  The
+// fastest run is kept.  The candidates give identical results (the shape
+// decides only which warp does which part of the same sums, and when).
 static int tune_tiles(boruta_session* s) {
   struct Shape {
     uint32_t gw;
-    int64_t bb;
+    int64_t bb;  // -1: per level (lvl_bb, lvl_bl)
     int32_t bl;
   };
   const int64_t p = s->p, T = s->max_iter;
@@ -582,14 +624,26 @@ static int tune_tiles(boruta_session* s) {
   CK(cudaEventCreate(&e[1]));
   s->tune_gw.clear();
   s->tune_bb.clear();
-  s->tune_ms.clear();
-  const bool graph = s->graph;
-  s->graph = false;
   s->tune_bl.clear();
+  s->tune_ms.clear();
+  s->tune_lvl_ms.clear();
+  const bool graph = s->graph;
+  s->graph = false;  // level events need stream launches
+  const int policy0 = s->band_policy;
+  std::vector<int64_t> comb_bb;
+  std::vector<int32_t> comb_bl;
   auto run = [&](const Shape& sh) -> int {
     s->d.group_work = sh.gw;
-    s->band_bytes = sh.bb;
-    s->d.band_launch = sh.bl;
+    if (sh.bb < 0) {
+      s->lvl_bb = comb_bb;
+      s->lvl_bl = comb_bl;
+      s->band_policy = policy0;
+    } else {
+      s->lvl_bb.clear();
+      s->lvl_bl.clear();
+      s->band_bytes = sh.bb;
+      s->band_policy = sh.bl ? 1 : 2;
+    }
     CK(cudaEventRecord(e[0], s->st));
     int r = enqueue_iteration(s, t0 + 1, s->st);
     if (!r) {
@@ -603,8 +657,9 @@ static int tune_tiles(boruta_session* s) {
     if (!r) {
       s->tune_gw.push_back(sh.gw);
       s->tune_bb.push_back(sh.bb);
-      s->tune_bl.push_back(sh.bl);
+      s->tune_bl.push_back(sh.bb < 0 ? -1 : sh.bl);
       s->tune_ms.push_back(ms);
+      s->tune_lvl_ms.push_back(s->level_ms);
     }
     return r;
   };
@@ -614,14 +669,25 @@ static int tune_tiles(boruta_session* s) {
       if (s->tune_ms[i] < s->tune_ms[b]) b = i;
     return b;
   };
-  for (int64_t bb : {int64_t{12} << 20, int64_t{24} << 20, int64_t{48} << 20, int64_t{96} << 20, int64_t{1} << 40})
+  for (int64_t bb : {int64_t{12} << 20, int64_t{24} << 20, int64_t{48} << 20, int64_t{96} << 20,
+                     int64_t{192} << 20, int64_t{1} << 40})
     for (int32_t bl : {0, 1})
-      if (!rc && !(bl == 1 && bb > (int64_t{96} << 20))) rc = run(Shape{kGroupWork, bb, bl});
+      if (!rc && !(bl == 1 && bb > (int64_t{192} << 20))) rc = run(Shape{kGroupWork, bb, bl});
+  const size_t uniform = rc ? 0 : s->tune_ms.size();
   if (!rc) {
-    const size_t b = best_index();
-    const Shape at{0u, s->tune_bb[b], s->tune_bl[b]};
-    for (uint32_t gw : {4096u, 16384u})
-      if (!rc) rc = run(Shape{gw, at.bb, at.bl});
+    // per level: the shape of the uniform run whose level was fastest
+    const int D = s->d.D;
+    comb_bb.assign(D, kBandBytes);
+    comb_bl.assign(D, 0);
+    for (int l = 0; l < D; ++l) {
+      size_t b = 0;
+      for (size_t i = 1; i < uniform; ++i)
+        if (s->tune_lvl_ms[i].size() > static_cast<size_t>(l) && s->tune_lvl_ms[i][l] < s->tune_lvl_ms[b][l]) b = i;
+      comb_bb[l] = s->tune_bb[b];
+      comb_bl[l] = s->tune_bl[b];
+    }
+    for (uint32_t gw : {kGroupWork, 4096u, 16384u})
+      if (!rc) rc = run(Shape{gw, -1, 0});
   }
   cudaEventDestroy(e[0]);
   cudaEventDestroy(e[1]);
@@ -629,8 +695,16 @@ static int tune_tiles(boruta_session* s) {
   if (rc) return rc;
   const size_t best = best_index();
   s->d.group_work = s->tune_gw[best];
-  s->band_bytes = s->tune_bb[best];
-  s->d.band_launch = s->tune_bl[best];
+  if (s->tune_bb[best] < 0) {
+    s->lvl_bb = comb_bb;
+    s->lvl_bl = comb_bl;
+    s->band_policy = policy0;
+  } else {
+    s->lvl_bb.clear();
+    s->lvl_bl.clear();
+    s->band_bytes = s->tune_bb[best];
+    s->band_policy = s->tune_bl[best] ? 1 : 2;
+  }
   s->tune_chosen = static_cast<int>(best);
   return 0;
 }
@@ -809,6 +883,26 @@ int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried,
     if (band_launch) band_launch[i] = s->tune_bl[i];
     if (ms) ms[i] = s->tune_ms[i];
   }
+  return 0;
+}
+
+int boruta_session_tuning_levels(boruta_session* s, int32_t capacity, int32_t* n_levels, int64_t* band_bytes,
+                                 int32_t* band_launch, double* level_ms) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  if (capacity < 0) return fail(BORUTA_EINVAL, "capacity < 0");
+  const int D = s->d.D;
+  if (n_levels) *n_levels = D;
+  for (int l = 0; l < D && l < capacity; ++l) {
+    const bool per = l < static_cast<int>(s->lvl_bb.size());
+    const bool used = l < static_cast<int>(s->used_bl.size());
+    if (band_bytes) band_bytes[l] = per ? s->lvl_bb[l] : s->band_bytes;
+    if (band_launch) band_launch[l] = used ? s->used_bl[l] : -1;
+  }
+  if (level_ms)
+    for (size_t i = 0; i < s->tune_lvl_ms.size(); ++i)
+      for (int l = 0; l < D && l < capacity; ++l)
+        level_ms[i * static_cast<size_t>(capacity) + l] =
+            l < static_cast<int>(s->tune_lvl_ms[i].size()) ? s->tune_lvl_ms[i][l] : 0.0;
   return 0;
 }
 

@@ -60,6 +60,7 @@ struct Dev {
   uint64_t* items_u;             // [item_cap] (node rank, slot, feature) per item; each node's
                                  //   mtry items together, ordered by feature band
   uint64_t* items_s;             // [item_cap] groups (node rank, first item, count), by band
+  uint64_t* items_b;             // [item_cap] per group: its node's row-buffer offset << 24 | rows
   void* fbest;                   // [item_cap] packed best candidate per (node rank, slot)
   uint32_t* band_cnt;            // [kMaxBands + 1] groups per band, then cursors; last: total
   uint64_t item_cap;
@@ -95,7 +96,7 @@ constexpr int64_t kBandBytes = 48ll << 20;  // default column bytes per feature 
 constexpr uint64_t kMaxItems = 128ull << 20;  // plan buffer capacity (items)
 constexpr int kMaxIterations = 126;          // max_iter limit (exact binomial tails in 128 bits)
 #ifndef BORUTA_STAGED_ROWS
-#define BORUTA_STAGED_ROWS 128
+#define BORUTA_STAGED_ROWS 64
 #endif
 constexpr uint32_t kRegRows = BORUTA_STAGED_ROWS;  // node rows a warp stages in shared memory
 constexpr uint32_t kGroupWork = 8192;        // default row x feature work per group for larger nodes
@@ -133,12 +134,16 @@ void launch_stats_decide(const Dev& d, cudaStream_t st);
 // Warp-private histogram layout.  A lane scans 8 consecutive bins, so one
 // padding slot follows every 8 bins: lane l's block then starts at a bank
 // offset coprime with 32 and the scan reads are free of bank conflicts.
-//   classification: count(b, k) at word b*C + k + b/8
+//   classification: count(b, k) at word b*C + k + b/8, or, packed (a node
+//                   of total weight below 4096 and at most five classes),
+//                   all classes of bin b in the u64 b + b/8
 //   regression:     weight(b) at word b + b/8; sum(b) at u64 b + b/8 after the weights
 __host__ __device__ inline int hist_words_n(int B) { return (B + (B >> 3) + 2) & ~1; }
 __host__ __device__ inline size_t hist_smem_per_warp(int kind, int C, int B) {
-  const size_t b = kind == 0 ? (static_cast<size_t>(B) * C + (B >> 3) + 1) * 4
-                             : static_cast<size_t>(hist_words_n(B)) * 4 + static_cast<size_t>(B + (B >> 3) + 1) * 8;
+  const size_t packed = static_cast<size_t>(B + (B >> 3) + 1) * 8;
+  size_t b = kind == 0 ? (static_cast<size_t>(B) * C + (B >> 3) + 1) * 4
+                       : static_cast<size_t>(hist_words_n(B)) * 4 + packed;
+  if (b < packed) b = packed;
   return (b + 15) & ~static_cast<size_t>(15);
 }
 // per warp: the histogram, a node's row entries (up to kRegRows), then the

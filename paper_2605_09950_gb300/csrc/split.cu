@@ -16,10 +16,12 @@
 //                   in, cut into (node, band) groups sorted by band, so that
 //                   the columns being gathered at any moment fit in L2;
 //     k_items_band  one warp per group: per feature a warp-private
-//                   shared-memory histogram (entries of nodes of <= 128 rows
-//                   staged once per group), a float pre-screen over the
-//                   non-empty bins, and the feature's exact best candidate,
-//                   kept as the integers that define it;
+//                   shared-memory histogram (entries of nodes of <= 64 rows
+//                   staged once per group; class weights packed 12 bits
+//                   each into one 64-bit word per bin when they fit), a
+//                   float pre-screen over the non-empty bins, and the
+//                   feature's exact best candidate, kept as the integers
+//                   that define it;
 //     k_finalize_band  one warp per node: float screen of its features'
 //                   candidates, exact argmax, split record and partition.
 //   larger nodes, grouped path (split_path = 1, or mtry >= 2^14): k_items
@@ -92,6 +94,8 @@ __device__ __forceinline__ uint32_t ld_keep(const uint8_t* a, uint64_t pol) {
 }
 
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* a) { return __ldcs(a); }
+
+__device__ __forceinline__ void prefetch_l2(const void* a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
 
 // Row entries: row << 8 | low byte.  Classification: low byte = y << 5 | w
 // (label < 8, bootstrap count < 32); regression: low byte = w (< 256).
@@ -739,8 +743,8 @@ __device__ __forceinline__ void hist_clear(const Dev& d, uint32_t* hw) {
   const int lane = threadIdx.x & 31;
   const int C = d.C, B = d.B;
   if (KIND == 0) {
-    const int words = (B * C + (B >> 3) + 4) & ~3;  // within the 16-byte aligned per-warp block
-    for (int i = lane; i < (words >> 2); i += 32) reinterpret_cast<uint4*>(hw)[i] = make_uint4(0u, 0u, 0u, 0u);
+    const int vecs = static_cast<int>(hist_smem_per_warp(0, C, B) / 16);  // either layout, whole
+    for (int i = lane; i < vecs; i += 32) reinterpret_cast<uint4*>(hw)[i] = make_uint4(0u, 0u, 0u, 0u);
   } else {
     uint32_t* hn = hw;
     unsigned long long* hs = reinterpret_cast<unsigned long long*>(hw + hist_words_n(B));
@@ -1012,10 +1016,9 @@ __device__ __forceinline__ void scan_screen(const Dev& d, const NodeInfo<CM>& nd
 // Exact best among the candidates whose float score is at least thr (all
 // lanes; only a lane whose own best is inside the window revisits its bins).
 template <int KIND, int CM>
-__device__ void scan_exact(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* hw, const Screen<CM>& S, float thr,
+__device__ void scan_exact(int C, int B, const NodeInfo<CM>& nd, const uint32_t* hw, const Screen<CM>& S, float thr,
                            int feat, uint32_t tkey, Cand<CM>& out) {
   const int lane = threadIdx.x & 31;
-  const int C = ncls<CM>(d), B = d.B;
   const int b0 = lane * ((B + 31) >> 5);
   Cand<CM> mine;
   mine.valid = false;
@@ -1077,7 +1080,7 @@ __device__ float scan_hist(const Dev& d, const NodeInfo<CM>& nd, const uint32_t*
   const float mx = warp_max_f(S.lmax);
   out.valid = false;
   if (!exact || mx < 0.0f) return mx;
-  scan_exact<KIND, CM>(d, nd, hw, S, screen(mx), feat, tkey, out);
+  scan_exact<KIND, CM>(ncls<CM>(d), d.B, nd, hw, S, screen(mx), feat, tkey, out);
   return mx;
 }
 
@@ -1140,6 +1143,16 @@ __device__ __forceinline__ void unpack_cand(const PackedCand<CM>& p, const NodeI
   c.key = (tkey << 8) | (p.fb & 255u);
 }
 
+// The exact comparison of scan_pack when several candidates lie inside the
+// screen window: rare, so kept out of line (arguments by value).
+template <int KIND, int CM>
+__device__ __noinline__ void scan_exact_pack(int C, int B, const NodeInfo<CM> nd, const uint32_t* hw,
+                                             const Screen<CM> S, float thr, uint32_t f, PackedCand<CM>* dst) {
+  Cand<CM> c;
+  scan_exact<KIND, CM>(C, B, nd, hw, S, thr, static_cast<int>(f), 0u, c);
+  if ((threadIdx.x & 31) == 0) *dst = pack_cand<KIND, CM>(c);
+}
+
 // A feature's exact best candidate, packed, from its built histogram.  When
 // a single candidate lies inside the float screen window it is the exact
 // best and is packed as is; otherwise the candidates inside the window are
@@ -1179,10 +1192,204 @@ __device__ void scan_pack(const Dev& d, const NodeInfo<CM>& nd, const uint32_t* 
       *dst = p;
     }
   } else {
-    Cand<CM> c;
-    scan_exact<KIND, CM>(d, nd, hw, S, thr, static_cast<int>(f), 0u, c);
-    if (lane == 0) *dst = pack_cand<KIND, CM>(c);
+    scan_exact_pack<KIND, CM>(ncls<CM>(d), d.B, nd, hw, S, thr, f, dst);
   }
+}
+
+// ---- packed class histograms
+// A classification node of at most five classes whose total weight is below
+// 4096 keeps all class weights of a bin in one 64-bit word, 12 bits per
+// class (class k in bits 12k .. 12k+11).  Every partial sum of a bin or of a
+// prefix of bins is at most the node's total weight, so no field carries into
+// the next: one shared-memory add, load, scan step or store moves all the
+// classes of a bin.  Staged nodes (at most kRegRows rows of bootstrap count
+// below 32) always qualify.
+constexpr int kPkBits = 12;
+constexpr uint32_t kPkLimit = 1u << kPkBits;
+
+template <int KIND, int CM>
+__device__ __forceinline__ bool packed_ok(const Dev& d, const NodeInfo<CM>& nd) {
+  return KIND == 0 && CM <= 5 && !regs4(d, 0) && nd.n < kPkLimit;
+}
+
+// class weights of a packed word; returns their sum
+template <int CM>
+__device__ __forceinline__ uint32_t pk_unpack(unsigned long long v, uint32_t (&c)[CM], int C) {
+  uint32_t n = 0u;
+#pragma unroll
+  for (int k = 0; k < CM; ++k) {
+    c[k] = k < C ? static_cast<uint32_t>(v >> (kPkBits * k)) & (kPkLimit - 1u) : 0u;
+    n += c[k];
+  }
+  return n;
+}
+
+__device__ __forceinline__ unsigned long long pk_entry(uint32_t e) {
+  return static_cast<unsigned long long>(ent_w<0>(e)) << (kPkBits * ent_y(e));
+}
+
+// Adds up to 32 * kBatch rows (entries in registers) to a packed histogram.
+template <int kBatch>
+__device__ __forceinline__ void hist_add_pk(uint32_t r0, uint32_t len, const uint32_t (&e)[kBatch],
+                                            const uint8_t* col, unsigned long long* hp) {
+  const int lane = threadIdx.x & 31;
+  uint32_t b[kBatch];
+  const uint64_t pol = keep_policy();
+#pragma unroll
+  for (int q = 0; q < kBatch; ++q) {
+    const uint32_t r = r0 + q * 32 + lane;
+    b[q] = r < len ? ld_keep(col + (e[q] >> 8), pol) : 0u;
+  }
+#pragma unroll
+  for (int q = 0; q < kBatch; ++q)
+    if (r0 + q * 32 + lane < len) atomicAdd(&hp[b[q] + (b[q] >> 3)], pk_entry(e[q]));
+}
+
+// Packed histogram of one feature over a node's rows, streamed from the row
+// buffer (the histogram is zero on entry).
+__device__ void build_hist_pk(int64_t base, uint32_t len, const uint32_t* rows, const uint8_t* col,
+                              unsigned long long* hp) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kBatch = BORUTA_STREAM_BATCH;
+  for (uint32_t r0 = 0; r0 < len; r0 += 32 * kBatch) {
+    uint32_t e[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const uint32_t r = r0 + q * 32 + lane;
+      e[q] = r < len ? ld_stream(rows + base + r) : 0u;
+    }
+    hist_add_pk<kBatch>(r0, len, e, col, hp);
+  }
+  __syncwarp();
+}
+
+// Packed histogram of one feature over a staged node (entries in ebuf, the
+// feature's bins gathered into b; the histogram is zero on entry).
+__device__ __forceinline__ void hist_staged_pk(uint32_t len, const uint32_t* ebuf, const uint32_t (&b)[kRegRows / 32],
+                                               unsigned long long* hp) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) {
+    const uint32_t r = q * 32 + lane;
+    if (r < len) atomicAdd(&hp[b[q] + (b[q] >> 3)], pk_entry(ebuf[r]));
+  }
+  __syncwarp();
+}
+
+// Exact best among a packed histogram's candidates whose float score is at
+// least thr (several lie inside the screen window: rare, so kept out of line).
+// cand: the lane's candidate bins to revisit; pre: the warp prefix before them.
+// (Arguments by value: nothing of the caller's state has to live in memory.)
+template <int CM>
+__device__ __noinline__ void pk_exact(int C, int B, const NodeInfo<CM> nd, const unsigned long long* hp,
+                                      unsigned long long pre, uint32_t cand, float thr, uint32_t f,
+                                      PackedCand<CM>* dst) {
+  const int lane = threadIdx.x & 31;
+  const int b0 = lane * ((B + 31) >> 5);
+  Cand<CM> best;
+  best.valid = false;
+  unsigned long long cum = pre;
+  for (uint32_t m = cand; m; m &= m - 1) {
+    const int bb = b0 + __ffs(m) - 1;
+    cum += hp[bb + (bb >> 3)];
+    uint32_t cl[CM];
+    const uint32_t nL = pk_unpack<CM>(cum, cl, C);
+    if (nL < nd.n && score_class_f<CM>(cl, nd.cp, C, nL, nd.n) >= thr) {
+      Cand<CM> c;
+      make_class<CM>(c, cl, nd.cp, C, nL, nd.n);
+      c.feat = static_cast<int32_t>(f);
+      c.bin = bb;
+      c.key = static_cast<uint32_t>(bb);
+      if (better(c, best)) best = c;
+    }
+  }
+  Cand<CM> c;
+  warp_select<0, CM>(best, c);
+  if (lane == 0) *dst = pack_cand<0, CM>(c);
+}
+
+// scan_pack over a packed histogram, which it leaves zero.  Lane l owns bins
+// [l*bpl, (l+1)*bpl) as in scan_screen: it reads them all at once, scans
+// the warp's totals once for all classes, and scores only its non-empty
+// bins below the last (an empty bin repeats the partition of the nearest
+// non-empty bin below it, which wins the tie).
+template <int CM>
+__device__ void scan_pack_pk(const Dev& d, const NodeInfo<CM>& nd, unsigned long long* hp, uint32_t f,
+                             PackedCand<CM>* dst) {
+  const int lane = threadIdx.x & 31;
+  const int C = ncls<CM>(d), B = d.B;
+  const int bpl = (B + 31) >> 5;  // <= 8
+  const int b0 = lane * bpl;
+  uint32_t nz = 0u, cand = 0u;
+  unsigned long long tot = 0ull;
+  {
+    unsigned long long v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int bb = b0 + q;
+      v[q] = (q < bpl && bb < B) ? hp[bb + (bb >> 3)] : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (v[q] != 0ull) {
+        nz |= 1u << q;
+        tot += v[q];
+        if (b0 + q < B - 1) cand |= 1u << q;
+      }
+  }
+  const unsigned long long pre = static_cast<unsigned long long>(warp_excl_scan_i64(static_cast<long long>(tot), lane));
+  float lmax = -1.0f, s2 = -1.0f;
+  int bbest = 0;
+  unsigned long long cbest = 0ull, cum = pre;
+  for (uint32_t m = cand; m; m &= m - 1) {
+    const int bb = b0 + __ffs(m) - 1;
+    cum += hp[bb + (bb >> 3)];
+    uint32_t cl[CM];
+    const uint32_t nL = pk_unpack<CM>(cum, cl, C);
+    if (nL < nd.n) {
+      const float sc = score_class_f<CM>(cl, nd.cp, C, nL, nd.n);
+      if (sc > lmax) {
+        s2 = lmax;
+        lmax = sc;
+        bbest = bb;
+        cbest = cum;
+      } else if (sc > s2) {
+        s2 = sc;
+      }
+    }
+  }
+  const float mx = warp_max_f(lmax);
+  if (mx < 0.0f) {
+    if (lane == 0) {
+      PackedCand<CM> p;
+      p.fb = kLeaf;
+      p.nL = 0u;
+#pragma unroll
+      for (int k = 0; k < CM; ++k) p.cL[k] = 0u;
+      *dst = p;
+    }
+  } else {
+    const float thr = screen(mx);
+    const uint32_t mine = (lmax >= thr ? 1u : 0u) + (s2 >= thr ? 1u : 0u);
+    if (__reduce_add_sync(kFull, mine) == 1u) {
+      if (mine) {  // the only candidate inside the window is the exact best
+        PackedCand<CM> p;
+        uint32_t cl[CM];
+        p.fb = (f << 8) | static_cast<uint32_t>(bbest);
+        p.nL = pk_unpack<CM>(cbest, cl, C);
+#pragma unroll
+        for (int k = 0; k < CM; ++k) p.cL[k] = cl[k];
+        *dst = p;
+      }
+    } else {
+      pk_exact<CM>(C, B, nd, hp, pre, lmax >= thr ? cand : 0u, thr, f, dst);
+    }
+  }
+  for (uint32_t m = nz; m; m &= m - 1) {  // each lane clears its own bins, after its own reads
+    const int bb = b0 + __ffs(m) - 1;
+    hp[bb + (bb >> 3)] = 0ull;
+  }
+  __syncwarp();
 }
 
 // Histogram of one feature over a node of at most kRegRows rows whose entries
@@ -1403,7 +1610,9 @@ __global__ void __launch_bounds__(256) k_plan_scatter(Dev d, int level) {
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const int bpl = (d.nbands + 31) >> 5;
   for (uint32_t rank = gwarp; rank < nbig; rank += nwarps) {
-    const uint32_t len = reinterpret_cast<const NodeInfo<CM>*>(d.ninfo)[rank].len;
+    const NodeInfo<CM>* nd = reinterpret_cast<const NodeInfo<CM>*>(d.ninfo) + rank;
+    const uint32_t len = nd->len;
+    const uint64_t where = (static_cast<uint64_t>(nd->base) << 24) | len;  // N < 2^24
     const uint64_t* items = d.items_u + static_cast<uint64_t>(rank) * d.mtry;
     for (int b = lane; b < d.nbands; b += 32) cnt[b] = 0u;
     __syncwarp();
@@ -1426,8 +1635,10 @@ __global__ void __launch_bounds__(256) k_plan_scatter(Dev d, int level) {
       if (q >= bpl || b >= d.nbands || c[q] == 0u) continue;
       const uint32_t first = cnt[b], n = c[q], ng = (n + gc - 1) / gc;
       const uint32_t pos = atomicAdd(&d.band_cnt[b], ng);
-      for (uint32_t g = 0; g < ng; ++g)
+      for (uint32_t g = 0; g < ng; ++g) {
         d.items_s[pos + g] = pack_group(rank, first + g * gc, min(gc, n - g * gc));
+        d.items_b[pos + g] = where;
+      }
     }
     __syncwarp();
   }
@@ -1443,6 +1654,7 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
   uint32_t* hw = smem + warp * (split_smem_per_warp(d.kind, d.C, d.B) / 4);
   uint32_t* ebuf = hw + hist_smem_per_warp(d.kind, d.C, d.B) / 4;
   uint32_t* occ = ebuf + kRegRows;
+  unsigned long long* hp = reinterpret_cast<unsigned long long*>(hw);  // the packed layout
   if (chunk_nodes(d, level) == 0u) return;
   hist_clear<KIND>(d, hw);  // from here on a feature leaves the histogram zeroed
   if (lane < 9) occ[lane] = 0u;
@@ -1457,31 +1669,66 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
   // is large (it is then mostly empty); small histograms are read whole
   const bool sparse = d.B * (KIND ? 3 : ncls<CM>(d)) >= 512;
   unsigned long long bytes = 0;
-  for (uint32_t g = g0 + gwarp; g < g1; g += nwarps) {
-    const uint64_t gr = d.items_s[g];
+  // Software pipeline over the warp's groups: a group's record (node rank,
+  // items, and the node's row offset and size) is loaded one group ahead,
+  // so a group starts with the loads of its row entries, node totals and
+  // items all in flight at once, and the next staged node's entries are
+  // prefetched into L2 while this group's features run.
+  uint32_t g = g0 + gwarp;
+  uint64_t gr = 0ull, gb = 0ull;
+  if (g < g1) {
+    gr = d.items_s[g];
+    gb = d.items_b[g];
+  }
+  for (; g < g1; g += nwarps) {
+    const uint32_t gn = g + nwarps;
+    uint64_t gr_n = 0ull, gb_n = 0ull;
+    if (gn < g1) {
+      gr_n = d.items_s[gn];
+      gb_n = d.items_b[gn];
+    }
     const uint32_t rank = static_cast<uint32_t>(gr >> 28);
     const uint32_t first = static_cast<uint32_t>(gr >> 14) & 0x3FFFu;
     const uint32_t count = static_cast<uint32_t>(gr & 0x3FFFu) + 1u;
-    const NodeInfo<CM> nd = reinterpret_cast<const NodeInfo<CM>*>(d.ninfo)[rank];
-    const uint64_t* items = d.items_u + static_cast<uint64_t>(rank) * d.mtry + first;
-    PackedCand<CM>* out = reinterpret_cast<PackedCand<CM>*>(d.fbest) + static_cast<uint64_t>(rank) * d.mtry;
+    const uint32_t len = static_cast<uint32_t>(gb & 0xFFFFFFu);
     // A node of at most kRegRows rows: its entries are read once, into the
     // warp's shared-memory buffer, for all the group's features, and the
     // next feature's bins are gathered while this one's are counted and
     // scanned.  Larger nodes stream their entries per feature.
-    const bool staged = nd.len <= kRegRows;
+    const bool staged = len <= kRegRows;
+    uint32_t ev[kRegRows / 32];
     if (staged) {
-      for (uint32_t r = lane; r < nd.len; r += 32) ebuf[r] = ld_stream(rows_in + nd.base + r);
+      const uint32_t* src = rows_in + static_cast<int64_t>(gb >> 24);
+#pragma unroll
+      for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q) {
+        const uint32_t r = q * 32 + lane;
+        ev[q] = r < len ? ld_stream(src + r) : 0u;
+      }
+    }
+    const NodeInfo<CM> nd = reinterpret_cast<const NodeInfo<CM>*>(d.ninfo)[rank];
+    const uint64_t* items = d.items_u + static_cast<uint64_t>(rank) * d.mtry + first;
+    PackedCand<CM>* out = reinterpret_cast<PackedCand<CM>*>(d.fbest) + static_cast<uint64_t>(rank) * d.mtry;
+    uint64_t chunk = items[lane < count ? lane : 0u];  // items j..j+31 of the group, one per lane
+    if (staged) {
+#pragma unroll
+      for (int q = 0; q < static_cast<int>(kRegRows / 32); ++q)
+        if (q * 32 + lane < len) ebuf[q * 32 + lane] = ev[q];
       __syncwarp();
     }
-    uint64_t chunk = items[lane < count ? lane : 0u];  // items j..j+31 of the group, one per lane
+    const bool pk = packed_ok<KIND, CM>(d, nd);
     uint32_t bn[kRegRows / 32];
-    if (staged) gather_staged(column(d, static_cast<uint32_t>(__shfl_sync(kFull, chunk, 0) & 0x3FFFFFu)), nd.len,
+    if (staged) gather_staged(column(d, static_cast<uint32_t>(__shfl_sync(kFull, chunk, 0) & 0x3FFFFFu)), len,
                               ebuf, bn);
+    if (gn < g1) {  // the next staged node's entries, into L2 (one 128-byte line per lane)
+      const uint32_t len_n = static_cast<uint32_t>(gb_n & 0xFFFFFFu);
+      if (len_n <= kRegRows && lane * 32u < len_n)
+        prefetch_l2(rows_in + static_cast<int64_t>(gb_n >> 24) + lane * 32u);
+    }
     for (uint32_t j = 0; j < count; ++j) {
       const uint64_t it = __shfl_sync(kFull, chunk, j & 31);
       const uint32_t f = static_cast<uint32_t>(it & 0x3FFFFFu);
       if (j + 1 < count && ((j + 1) & 31) == 0) chunk = items[j + 1 + lane < count ? j + 1 + lane : j + 1];
+      PackedCand<CM>* dst = out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu);
       if (staged) {
         uint32_t b[kRegRows / 32];
 #pragma unroll
@@ -1489,6 +1736,13 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
         if (j + 1 < count)
           gather_staged(column(d, static_cast<uint32_t>(__shfl_sync(kFull, chunk, (j + 1) & 31) & 0x3FFFFFu)),
                         nd.len, ebuf, bn);
+        if constexpr (KIND == 0 && CM <= 5) {
+          if (pk) {
+            hist_staged_pk(nd.len, ebuf, b, hp);
+            scan_pack_pk<CM>(d, nd, hp, f, dst);
+            continue;
+          }
+        }
         hist_staged<KIND>(d, nd.len, ebuf, b, hw, occ, sparse);
         if (sparse) {
           const uint32_t mine = lane_occ(d, occ);
@@ -1501,6 +1755,13 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
           __syncwarp();
         }
       } else {
+        if constexpr (KIND == 0 && CM <= 5) {
+          if (pk) {
+            build_hist_pk(nd.base, nd.len, rows_in, column(d, f), hp);
+            scan_pack_pk<CM>(d, nd, hp, f, dst);
+            continue;
+          }
+        }
         build_hist<KIND, false>(d, nd.base, nd.len, rows_in, column(d, f), hw);
         scan_pack<KIND, CM>(d, nd, hw, f, out + (static_cast<uint32_t>(it >> 22) & 0x3FFFu));
         __syncwarp();
@@ -1513,6 +1774,8 @@ __global__ void __launch_bounds__(kSplitThreads, BORUTA_ITEMS_MINB) k_items_band
     // feature, and the node's row state once (entry read and rewritten, weight
     // and label, or the 8-byte target for regression)
     bytes += static_cast<unsigned long long>(nd.len) * (count + (first == 0u ? (KIND ? kRowStateReg : kRowStateClass) : 0u));
+    gr = gr_n;
+    gb = gb_n;
   }
   if (lane == 0 && bytes) atomicAdd(&d.counters[2], bytes);
 }

@@ -63,7 +63,7 @@ def test_default_opts(lib):
 @pytest.mark.parametrize("bad", [
     dict(N=0), dict(N=1 << 24), dict(n_bins=1), dict(n_bins=257), dict(max_iter=0), dict(max_iter=127),
     dict(max_depth=31), dict(n_trees=0), dict(alpha=0.0), dict(task=4), dict(mtry=-1),
-    dict(n_classes=9), dict(precision=2),
+    dict(n_classes=9), dict(precision=2), dict(band_launch=3), dict(band_launch=-1), dict(autotune=2),
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lib, bad):
     from paper_2605_09950_gb300 import boruta
@@ -73,7 +73,7 @@ def test_invalid_arguments_are_rejected_on_the_host(lib, bad):
     args = dict(task=0, n_trees=2, max_depth=3, mtry=0, n_bins=4, max_iter=3, alpha=0.01, seed=0, N=16)
     opts = dict(host_inputs=1)
     for k, v in bad.items():
-        (opts if k in ("n_classes", "precision") else args)[k] = v
+        (opts if k in ("n_classes", "precision", "band_launch", "autotune") else args)[k] = v
     with pytest.raises(boruta.BorutaError) as e:
         boruta.boruta_fit(X, y, **args, **opts)
     assert e.value.code == -1

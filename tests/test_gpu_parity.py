@@ -276,12 +276,12 @@ def test_graph_replay_matches_stream_launches(importance):
 
 @pytest.mark.parametrize("importance", [synth.TREEIMP, synth.PERMUT])
 def test_autotuned_tiles_give_the_same_run(importance):
-    """opts.autotune = 1: the first step times eleven histogram tile shapes
-    (band bytes x launch per chunk or per band, a single band, then group
-    work) on
-    iteration 1, restoring the state after each, and keeps the fastest; the
-    run is the same, bit for bit, as with the default shape, and the batched
-    form with autotune equals it too."""
+    """opts.autotune = 1: the first step times fourteen histogram tile shapes
+    (band bytes x launch per chunk or per band, a single band, then the
+    per-level combination at three group works) on iteration 1, restoring
+    the state after each, and keeps the fastest; the run is the same, bit for
+    bit, as with the default shape, and the batched form with autotune equals
+    it too."""
     import torch
 
     from paper_2605_09950_gb300 import boruta
@@ -298,8 +298,13 @@ def test_autotuned_tiles_give_the_same_run(importance):
     for key in ("decision", "hits", "imp_history", "shadow_max", "iterations"):
         np.testing.assert_array_equal(ra[key], rb[key], err_msg=key)
     tried, chosen = B.tuning()
-    assert len(tried) == 11 and 0 <= chosen < 11 and all(ms > 0 for _, _, _, ms in tried)
-    assert {gw for gw, _, _, _ in tried} == {4096, 8192, 16384} and {bl for _, _, bl, _ in tried} == {0, 1}
+    assert len(tried) == 14 and 0 <= chosen < 14 and all(ms > 0 for _, _, _, ms in tried)
+    assert {gw for gw, _, _, _ in tried} == {4096, 8192, 16384} and {bl for _, _, bl, _ in tried} == {-1, 0, 1}
+    assert [bb for _, bb, _, _ in tried[11:]] == [-1, -1, -1]
+    bb, bl, lm = B.tuning_levels()
+    assert len(bb) == w.max_depth and lm.shape == (14, w.max_depth)
+    uniform = [b for _, b, _, _ in tried[:11]]
+    assert all(b in uniform for b in bb) and all(x in (0, 1) for x in bl)
     assert A.tuning() == ([], -1)
     params = w.params()
     job = dict(X=torch.from_numpy(w.X).cuda(), y=torch.from_numpy(w.y).cuda(), N=w.N, **params)
@@ -409,10 +414,14 @@ def test_band_path_in_many_chunks(case):
     ref.step()
     per_band = session(w, chunk_nodes=3, band_launch=1)  # one histogram launch per band
     per_band.step()
+    per_chunk = session(w, chunk_nodes=3, band_launch=2)  # one per chunk at every level
+    per_chunk.step()
     for what, dt in ((boruta.DUMP_NODES, boruta.NODE_DTYPE), (boruta.DUMP_IMP, np.float64),
                      (boruta.DUMP_STAT, np.float64)):
         np.testing.assert_array_equal(S.dump(what, dt), ref.dump(what, dt))
         np.testing.assert_array_equal(per_band.dump(what, dt), ref.dump(what, dt))
+        np.testing.assert_array_equal(per_chunk.dump(what, dt), ref.dump(what, dt))
+    assert set(per_band.tuning_levels()[1]) == {1} and set(per_chunk.tuning_levels()[1]) == {0}
     levels = S.dump(boruta.DUMP_LEVELS, np.float64).reshape(-1, 3)
     assert levels[:, 0].max() > 3 * 3  # some level held more than three chunks of nodes
 

@@ -54,12 +54,23 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch of the histogram kernel, from the ncu
 # capture named beside it, valid only for the kernel source it was taken on
 # (sha-256 prefix of csrc/split.cu); the line reports null otherwise.
-TRAFFIC = {}
+# DRAM bytes (read + write) of the histogram kernel per tree level, from one
+# ncu capture of a whole iteration (the profile named), valid only while the
+# kernel's and its launch code's sources hash to sources_sha16
+TRAFFIC = {
+    "multiclass_N1000000_p500": {"bytes_per_launch": (585.1e9 + 63.12e9) / 20, "sources_sha16": "42996fcf50cdfd8b",
+                                 "profile": "profiles/k_items_band_multiclass_N1000000_p500.md"},
+}
 
 
 def kernel_source_sha16():
-    with open(os.path.join(ROOT, "paper_2605_09950_gb300", "csrc", "split.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the histogram kernel's sources and of the host code that sets
+    its launches (a recorded traffic figure holds only for these)."""
+    h = hashlib.sha256()
+    for name in ("split.cu", "engine.cuh", "api.cu"):
+        with open(os.path.join(ROOT, "paper_2605_09950_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -307,6 +318,7 @@ class Stepper:
         self.S, self.max_iter = S, max_iter
         self.fresh = S.read()
         self.t, self.done = 0, False
+        self.launches = 0  # the library's kernels launched by this stepper's steps
 
     def ready(self):
         if self.done:
@@ -318,6 +330,7 @@ class Stepper:
 
     def step(self):
         und = self.S.step()
+        self.launches += self.S.kernel_launches()
         self.t += 1
         self.done = und == 0 or self.t >= self.max_iter
 
@@ -403,7 +416,9 @@ def run_gpu(args):
             snap.update(S.read())
             snap["imp"] = S.dump(boruta.DUMP_IMP, np.float64)
 
+    launches0 = R.launches
     step_ms = timed_steps(R, args.steps, stream, flush, collect)
+    timed_launches = R.launches - launches0
     levels = S.dump(boruta.DUMP_LEVELS, np.float64).reshape(-1, 3)
     value, total_ms = combine_ranks(sum(step_ms), args.steps, dist)
     clocks = stop_clock_sampler(proc, fh, clk_path, local) if rank == 0 else None
@@ -456,7 +471,7 @@ def run_gpu(args):
     achieved = ks["hist_bytes"] / (ks["hist_ms"] / 1000.0) / 1e9 if ks["hist_ms"] > 0 else 0.0
     split_gbs = ks["split_bytes"] / (ks["split_ms"] / 1000.0) / 1e9 if ks["split_ms"] > 0 else 0.0
     prof = TRAFFIC.get(w.name)
-    traffic = prof["bytes_per_launch"] if prof and prof["split_cu_sha16"] == kernel_source_sha16() \
+    traffic = prof["bytes_per_launch"] if prof and prof["sources_sha16"] == kernel_source_sha16() \
         and not args.trees else None
     permut = importance == "permut_oob"
     walks = None
@@ -467,9 +482,6 @@ def run_gpu(args):
                  "l2_bytes_per_visit": "17 B: the two children's split words and child indices (16 B) "
                                        "loaded with the row's bin of the tested feature (1 B)",
                  "kernels": "k_permut_pi + k_permut + k_permut_final (CUDA events around the stage)"}
-    # per step: gather + shadow + 2 bootstrap; per level 6 + 5 per band chunk (one chunk
-    # unless the level's larger nodes overflow the plan buffers); importance 2-3; stats + decide
-    per_step_launches = 4 + 11 * w.max_depth + (3 if permut else 1) + 2
     line = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -509,7 +521,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_iters,
                 "d2h_bytes_per_step": d2h / e2e_iters, "iterations": e2e_iters,
                 "note": "boruta_fit with host X/y: session setup, upload, iterations 1..k, readback"},
-        "gpu_launches": per_step_launches * args.steps,
+        "gpu_launches": timed_launches,
         "clocks": clocks,
     }
     if cpu is not None:

@@ -277,6 +277,12 @@ int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried,
 int boruta_session_tuning_levels(boruta_session* s, int32_t capacity, int32_t* n_levels, int64_t* band_bytes,
                                  int32_t* band_launch, double* level_ms);
 
+/* The number of this library's kernels the last step launched (the whole
+ * iteration: shadows, bootstrap, every level's split kernels, the importance
+ * stage, the statistic and the test); 0 before the first step.  A step
+ * replayed from a graph launches the same kernels. */
+int boruta_session_kernel_launches(boruta_session* s, int64_t* kernels);
+
 /* Timing of the last step's importance stage (Alg. 2 normalisation, or the
  * Alg. 3 tree walks and their reduction), from CUDA events on the session's
  * stream (0 when the step was replayed from a graph), and the number of

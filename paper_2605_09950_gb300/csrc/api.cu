@@ -105,6 +105,7 @@ struct boruta_session {
   double split_ms = 0.0;
   std::vector<double> level_ms, level_hist_ms;
   int split_launches = 0;
+  int64_t iter_kernels = 0;  // kernels the last enqueued iteration launched
   double split_bytes = 0.0;
   std::vector<cudaEvent_t> hev;  // around the histogram kernel of each level
   double hist_ms = 0.0, hist_bytes = 0.0;
@@ -366,6 +367,8 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   if ((rc = s->alloc(&d.small, level_cap))) return rc;
   if ((rc = s->alloc(&d.nsmall, max_depth + 2))) return rc;
   if ((rc = s->alloc(&d.ntiny, max_depth + 2))) return rc;
+  if ((rc = s->alloc(&d.micro, level_cap))) return rc;
+  if ((rc = s->alloc(&d.nmicro, max_depth + 2))) return rc;
   d.small_cap = static_cast<uint32_t>(level_cap);
   uint8_t* cand = nullptr;
   if ((rc = s->alloc(&cand, big_cap * kItemsPerNode * cand_bytes(split_variant(d.kind, d.C))))) return rc;
@@ -530,6 +533,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   CK(cudaMemsetAsync(d.work, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.nsmall, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.ntiny, 0, (d.D + 2) * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(d.nmicro, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.lvl_cnt, 0, (d.D + 2) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(d.counters, 0, 4 * sizeof(unsigned long long), st));
 
@@ -539,11 +543,12 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
     if (e_ != cudaSuccess) return fail(BORUTA_ECUDA, "launching %s: %s", what, cudaGetErrorString(e_)); \
   } while (0)
   CK_LAUNCH("(before the iteration)");
-  launch_gather_live(d, st);
+  int64_t nk = 0;  // kernels launched by this iteration
+  nk += launch_gather_live(d, st);
   CK_LAUNCH("k_gather_live");
-  launch_shadow(d, st);
+  nk += launch_shadow(d, st);
   CK_LAUNCH("k_shadow");
-  launch_bootstrap(d, s->tree_grid, st);
+  nk += launch_bootstrap(d, s->tree_grid, st);
   CK_LAUNCH("bootstrap kernels");
   for (int level = 0; level < d.D; ++level) {
     // grids sized to what the level can hold (every split kernel loops over
@@ -564,31 +569,32 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
     }
     s->used_bw[level] = dl.band_w;
     s->used_bl[level] = dl.band_launch;
-    launch_split(dl, level, std::max(gs, 1), gi, big, s->split_smem, st, s->st2, s->fork, s->join,
-                 timed ? s->hev[2 * level] : nullptr, timed ? s->hev[2 * level + 1] : nullptr);
+    nk += launch_split(dl, level, std::max(gs, 1), gi, big, s->split_smem, st, s->st2, s->fork, s->join,
+                       timed ? s->hev[2 * level] : nullptr, timed ? s->hev[2 * level + 1] : nullptr);
     CK_LAUNCH("split kernels");
     if (timed) CK(cudaEventRecord(s->ev[2 * level + 1], st));
-    launch_children(d, level, st);
+    nk += launch_children(d, level, st);
     CK_LAUNCH("next-level kernels");
   }
   if (timed) CK(cudaEventRecord(s->iev[0], st));
   if (d.permut_form == 1)
-    launch_forest_permut(d, s->permut_grid, st);
+    nk += launch_forest_permut(d, s->permut_grid, st);
   else if (d.permut)
-    launch_permut(d, s->permut_grid, s->walk_grid, st);
+    nk += launch_permut(d, s->permut_grid, s->walk_grid, st);
   else
-    launch_treeimp(d, s->tree_grid, st);
+    nk += launch_treeimp(d, s->tree_grid, st);
   CK_LAUNCH("importance kernels");
   if (timed) CK(cudaEventRecord(s->iev[1], st));
   if (d.permut_form == 1) {  // one importance row for the forest: it is the hit statistic
     Dev d1 = d;
     d1.M = 1;
     d1.stat = 1;
-    launch_stats_decide(d1, st);
+    nk += launch_stats_decide(d1, st);
   } else {
-    launch_stats_decide(d, st);
+    nk += launch_stats_decide(d, st);
   }
   CK_LAUNCH("k_stats / k_decide");
+  s->iter_kernels = nk;
   CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->state_pin, d.state, s->p, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->counters_h, d.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -883,6 +889,12 @@ int boruta_session_tuning(boruta_session* s, int32_t capacity, int32_t* n_tried,
     if (band_launch) band_launch[i] = s->tune_bl[i];
     if (ms) ms[i] = s->tune_ms[i];
   }
+  return 0;
+}
+
+int boruta_session_kernel_launches(boruta_session* s, int64_t* kernels) {
+  if (!s) return fail(BORUTA_EINVAL, "session is NULL");
+  if (kernels) *kernels = s->iter_kernels;
   return 0;
 }
 

@@ -53,7 +53,9 @@ struct Dev {
   uint32_t* big;                 // [big_cap] this level's active nodes with > 32 rows
   uint32_t* small;               // [level_cap] this level's active nodes with <= 32 rows
   uint32_t* nsmall;              // [D + 2] per level: number of 17..32-row nodes at the start of `small`
-  uint32_t* ntiny;               // [D + 2] per level: number of <= 16-row nodes at the end of `small`
+  uint32_t* ntiny;               // [D + 2] per level: number of 9..16-row nodes at the end of `small`
+  uint32_t* micro;               // [small_cap] this level's active nodes with <= 8 rows
+  uint32_t* nmicro;              // [D + 2] per level: number of them
   uint32_t small_cap;            // entries of `small`
   void* ninfo;                   // [big_cap] node totals of `big`, by rank
   void* cand;                    // [big_cap * kItemsPerNode] best candidate per grouped item
@@ -105,15 +107,15 @@ constexpr uint32_t kGroupWork = 8192;        // default row x feature work per g
 // label (1 + 1 B), or weight and 8-byte fixed-point target (regression)
 constexpr uint32_t kRowStateClass = 10, kRowStateReg = 17;
 
-// launchers (kernels.cu)
+// launchers (kernels.cu); each returns the number of kernels it launched
 void launch_validate(const Dev& d, cudaStream_t st);
-void launch_shadow(const Dev& d, cudaStream_t st);
-void launch_bootstrap(const Dev& d, int grid, cudaStream_t st);
+int launch_shadow(const Dev& d, cudaStream_t st);
+int launch_bootstrap(const Dev& d, int grid, cudaStream_t st);
 // split.cu: one level's split search.  Nodes are classified on `st`; the
 // small-node kernel then runs on `st2` while the larger-node kernels run on
 // `st` (fork/join through the two events).
 // hist_start/hist_end are recorded on `st` around the histogram kernel.
-void launch_split(const Dev& d, int level, int grid_small, int grid_big, uint64_t big_bound, size_t smem, cudaStream_t st,
+int launch_split(const Dev& d, int level, int grid_small, int grid_big, uint64_t big_bound, size_t smem, cudaStream_t st,
                   cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hist_start,
                   cudaEvent_t hist_end);
 size_t ninfo_bytes(int variant);
@@ -123,14 +125,14 @@ void split_kernel_ptrs(int variant, const void** ptrs, int* n);  // kernels taki
 const void* small_kernel_ptr(int variant);  // for its occupancy
 size_t cand_bytes(int variant);
 size_t packed_bytes(int variant);
-void launch_gather_live(const Dev& d, cudaStream_t st);
-void launch_children(const Dev& d, int level, cudaStream_t st);
-void launch_treeimp(const Dev& d, int grid, cudaStream_t st);
-void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st);
-void launch_forest_permut(const Dev& d, int grid, cudaStream_t st);
+int launch_gather_live(const Dev& d, cudaStream_t st);
+int launch_children(const Dev& d, int level, cudaStream_t st);
+int launch_treeimp(const Dev& d, int grid, cudaStream_t st);
+int launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st);
+int launch_forest_permut(const Dev& d, int grid, cudaStream_t st);
 const void* permut_kernel_ptr(int precision);  // for its occupancy
 size_t permut_smem_bytes(int D);                // its dynamic shared memory per block (128 threads)
-void launch_stats_decide(const Dev& d, cudaStream_t st);
+int launch_stats_decide(const Dev& d, cudaStream_t st);
 // Warp-private histogram layout.  A lane scans 8 consecutive bins, so one
 // padding slot follows every 8 bins: lane l's block then starts at a bank
 // offset coprime with 32 and the scan reads are free of bank conflicts.

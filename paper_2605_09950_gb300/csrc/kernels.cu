@@ -126,12 +126,13 @@ __global__ void k_gather_live(Dev d, int vec) {
   }
 }
 
-void launch_gather_live(const Dev& d, cudaStream_t st) {
+int launch_gather_live(const Dev& d, cudaStream_t st) {
   // 16-byte path: aligned base, ld a multiple of 16 and at least ldN bytes per column
   const int vec = (reinterpret_cast<uintptr_t>(d.X) % 16 == 0) && (d.ld % 16 == 0) && (d.ld >= d.ldN);
   int bx = ((vec ? d.ldN / 16 : d.N) + 255) / 256;
   if (bx > 16) bx = 16;
   k_gather_live<<<dim3(bx, d.p_live), 256, 0, st>>>(d, vec);
+  return 1;
 }
 
 // Xaug[p_live + c][i] = X[sigma_c(i)][live[c mod p_live]]; 16 rows per thread, one
@@ -158,10 +159,11 @@ __global__ void k_shadow(Dev d) {
   }
 }
 
-void launch_shadow(const Dev& d, cudaStream_t st) {
+int launch_shadow(const Dev& d, cudaStream_t st) {
   int bx = (d.N + 16 * 256 - 1) / (16 * 256);
   if (bx > 32) bx = 32;
   k_shadow<<<dim3(bx, d.n_sha), 256, 0, st>>>(d);
+  return 1;
 }
 
 // ============================================================ bootstrap
@@ -252,12 +254,13 @@ __global__ void k_boot_compact(Dev d) {
   }
 }
 
-void launch_bootstrap(const Dev& d, int grid, cudaStream_t st) {
+int launch_bootstrap(const Dev& d, int grid, cudaStream_t st) {
   int bx = (d.N + 255) / 256;
   if (bx > 64) bx = 64;
   int by = d.M < 4096 ? d.M : 4096;
   k_boot_count<<<dim3(bx, by), 256, 0, st>>>(d);
   k_boot_compact<<<grid, 256, 0, st>>>(d);
+  return 2;
 }
 
 // ============================================================ next level
@@ -352,9 +355,10 @@ __global__ void k_children(Dev d, int level) {
   }
 }
 
-void launch_children(const Dev& d, int level, cudaStream_t st) {
+int launch_children(const Dev& d, int level, cudaStream_t st) {
   k_count<<<kScanBlocks, 256, 0, st>>>(d, level);
   k_children<<<kScanBlocks, 256, 0, st>>>(d, level);
+  return 2;
 }
 
 // ============================================================ Alg. 2 normalisation
@@ -414,8 +418,9 @@ __global__ void k_treeimp_norm(Dev d) {
   }
 }
 
-void launch_treeimp(const Dev& d, int grid, cudaStream_t st) {
+int launch_treeimp(const Dev& d, int grid, cudaStream_t st) {
   k_treeimp_norm<<<grid, 256, 0, st>>>(d);
+  return 1;
 }
 
 // ============================================================ Alg. 3 on OOB rows
@@ -707,7 +712,7 @@ __global__ void k_permut_final(Dev d) {
   }
 }
 
-void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
+int launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
   k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
   k_transpose_rows<<<grid, 256, 0, st>>>(d);
   k_pack_nodes<<<grid, 256, 0, st>>>(d);
@@ -717,6 +722,7 @@ void launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
   else
     k_permut<1><<<walk_grid, 128, smem, st>>>(d);
   k_permut_final<<<grid, 256, 0, st>>>(d);
+  return 5;
 }
 
 size_t permut_smem_bytes(int D) { return 4 * permut_smem_per_warp(D); }
@@ -872,18 +878,22 @@ __global__ void k_fperm_final(Dev d) {
   }
 }
 
-void launch_forest_permut(const Dev& d, int grid, cudaStream_t st) {
+int launch_forest_permut(const Dev& d, int grid, cudaStream_t st) {
+  int n = 0;
   k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
   k_transpose_rows<<<grid, 256, 0, st>>>(d);
   cudaMemsetAsync(d.fbase, 0, static_cast<size_t>(d.N) * forest_k(d) * kCsaLimbs * sizeof(long long), st);
   k_fperm_base<<<grid, 256, 0, st>>>(d);
   k_fperm_base_mean<<<grid, 256, 0, st>>>(d);
+  n += 4;
   for (uint32_t r0 = 0; r0 < static_cast<uint32_t>(d.N); r0 += d.frows) {
     const uint32_t rows = min(d.frows, static_cast<uint32_t>(d.N) - r0);
     k_fperm_delta<<<grid, 256, 0, st>>>(d, r0, rows);
     k_fperm_loss<<<grid, 256, 0, st>>>(d, r0, rows);
+    n += 2;
   }
   k_fperm_final<<<(d.p_aug + 255) / 256, 256, 0, st>>>(d);
+  return n + 1;
 }
 
 // ============================================================ Alg. 1: statistic, hits, test
@@ -985,9 +995,10 @@ __global__ void k_decide(Dev d) {
   if (threadIdx.x == 0) d.status[1] = scnt[0];
 }
 
-void launch_stats_decide(const Dev& d, cudaStream_t st) {
+int launch_stats_decide(const Dev& d, cudaStream_t st) {
   k_stats<<<(d.p_aug + 127) / 128, 128, 0, st>>>(d);
   k_decide<<<1, 1024, 0, st>>>(d);
+  return 2;
 }
 
 // ============================================================ primitives for parity checks

@@ -402,12 +402,13 @@ struct SmallPlanes {
 };
 
 // A small node's rows sit one per lane in a segment of SEG lanes: the whole
-// warp (SEG = 32, nodes of 17..32 rows) or a half warp (SEG = 16: two nodes
-// of <= 16 rows per warp, one in each half).  Segment helpers: the lanes'
-// mask, and reductions that stay inside the segment.
+// warp (SEG = 32, nodes of 17..32 rows), a half warp (SEG = 16: two nodes of
+// 9..16 rows per warp) or a quarter warp (SEG = 8: four nodes of <= 8 rows).
+// Segment helpers: the lanes' mask, and reductions that stay inside the
+// segment.
 template <int SEG>
 __device__ __forceinline__ unsigned seg_mask() {
-  return SEG == 32 ? kFull : (0xFFFFu << ((threadIdx.x & 31) & 16));
+  return SEG == 32 ? kFull : (((1u << SEG) - 1u) << ((threadIdx.x & 31) & (32 - SEG)));
 }
 
 template <int SEG>
@@ -419,10 +420,13 @@ __device__ __forceinline__ float seg_max_f(float v) {
 
 template <int SEG>
 __device__ __forceinline__ uint32_t seg_sum_u32(uint32_t v) {
-  if (SEG == 32) return __reduce_add_sync(kFull, v);
+  if constexpr (SEG == 32) {
+    return __reduce_add_sync(kFull, v);
+  } else {
 #pragma unroll
-  for (int off = SEG / 2; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-  return v;
+    for (int off = SEG / 2; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+  }
 }
 
 template <int SEG>
@@ -593,8 +597,9 @@ __device__ void small_feature(const NodeInfo<CM>& nd, int C, int B, bool v, uint
 }
 
 // One thread per node of the level: leaves are marked, active nodes are
-// listed as tiny (<= 16 rows, from the end of `small`), small (17..32 rows,
-// from its start) or larger (warp-aggregated appends).
+// listed as micro (<= 8 rows, in `micro`), tiny (9..16 rows, from the end of
+// `small`), small (17..32 rows, from its start) or larger (warp-aggregated
+// appends).
 template <int KIND, int CM>
 __global__ void __launch_bounds__(256) k_classify(Dev d, int level) {
   const int lane = threadIdx.x & 31;
@@ -602,30 +607,33 @@ __global__ void __launch_bounds__(256) k_classify(Dev d, int level) {
   for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < lcount;
        base += gridDim.x * blockDim.x) {
     const uint32_t idx = base + lane;
-    int cls = 0;  // 0 none, 1 small, 2 larger, 3 tiny
+    int cls = 0;  // 0 none, 1 small, 2 larger, 3 tiny, 4 micro
     uint32_t k = 0;
     if (idx < lcount) {
       k = loff + idx;
       NodeInfo<CM> nd;
       if (load_node<KIND, CM>(d, k, level, nd))
-        cls = nd.len > 32u ? 2 : (nd.len > 16u ? 1 : 3);
+        cls = nd.len > 32u ? 2 : (nd.len > 16u ? 1 : (nd.len > 8u ? 3 : 4));
       else
         d.nd_split[k] = kLeaf;
     }
     const unsigned ms = __ballot_sync(kFull, cls == 1), mb = __ballot_sync(kFull, cls == 2),
-                   mt = __ballot_sync(kFull, cls == 3);
-    uint32_t s0 = 0, b0 = 0, t0 = 0;
+                   mt = __ballot_sync(kFull, cls == 3), mm = __ballot_sync(kFull, cls == 4);
+    uint32_t s0 = 0, b0 = 0, t0 = 0, m0 = 0;
     if (lane == 0) {
       if (ms) s0 = atomicAdd(&d.nsmall[level], static_cast<uint32_t>(__popc(ms)));
       if (mb) b0 = atomicAdd(&d.work[level], static_cast<uint32_t>(__popc(mb)));
       if (mt) t0 = atomicAdd(&d.ntiny[level], static_cast<uint32_t>(__popc(mt)));
+      if (mm) m0 = atomicAdd(&d.nmicro[level], static_cast<uint32_t>(__popc(mm)));
     }
     s0 = __shfl_sync(kFull, s0, 0);
     b0 = __shfl_sync(kFull, b0, 0);
     t0 = __shfl_sync(kFull, t0, 0);
+    m0 = __shfl_sync(kFull, m0, 0);
     if (cls == 1) d.small[s0 + __popc(ms & lanemask_lt())] = k;
     if (cls == 2) d.big[b0 + __popc(mb & lanemask_lt())] = k;
     if (cls == 3) d.small[d.small_cap - 1u - (t0 + __popc(mt & lanemask_lt()))] = k;
+    if (cls == 4) d.micro[m0 + __popc(mm & lanemask_lt())] = k;
   }
 }
 
@@ -713,8 +721,9 @@ __device__ void small_node(const Dev& d, int level, uint32_t k, uint8_t* sbin, u
   }
 }
 
-// SEG = 16: one warp per pair of tiny nodes (a half warp each);
-// SEG = 32: one warp per small node.
+// SEG = 8: one warp per four micro nodes (a quarter warp each); SEG = 16:
+// one warp per pair of tiny nodes (a half warp each); SEG = 32: one warp per
+// small node.
 template <int KIND, int CM, int SEG>
 __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, int level) {
   __shared__ uint8_t sbins[8][kSmallAhead * 32];
@@ -723,7 +732,14 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_split_small(Dev d, i
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned long long bytes = 0;
-  if (SEG == 16) {
+  if (SEG == 8) {
+    const uint32_t nm = d.nmicro[level], nquads = (nm + 3u) / 4u;
+    for (uint32_t idx = gwarp; idx < nquads; idx += nwarps) {
+      const uint32_t t = 4u * idx + static_cast<uint32_t>(lane >> 3);
+      const uint32_t k = t < nm ? d.micro[t] : kNoNode;
+      small_node<KIND, CM, SEG>(d, level, k, sbin, bytes);
+    }
+  } else if (SEG == 16) {
     const uint32_t nt = d.ntiny[level], npairs = (nt + 1u) / 2u;
     for (uint32_t idx = gwarp; idx < npairs; idx += nwarps) {
       const uint32_t t = 2u * idx + static_cast<uint32_t>(lane >> 4);
@@ -1913,13 +1929,15 @@ __global__ void __launch_bounds__(256, BORUTA_SMALL_MINB) k_finalize(Dev d, int 
 }
 
 template <int KIND, int CM>
-void launch_level(const Dev& d, int level, int grid_small, int grid_items, uint64_t big_bound, size_t smem,
-                  cudaStream_t st, cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hist_start,
-                  cudaEvent_t hist_end) {
+int launch_level(const Dev& d, int level, int grid_small, int grid_items, uint64_t big_bound, size_t smem,
+                 cudaStream_t st, cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hist_start,
+                 cudaEvent_t hist_end) {
+  int n = 4;  // k_classify and the three small-node kernels
   k_classify<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
   // small nodes on st2, concurrently with the larger-node kernels on st
   cudaEventRecord(fork, st);
   cudaStreamWaitEvent(st2, fork, 0);
+  k_split_small<KIND, CM, 8><<<grid_small, 256, 0, st2>>>(d, level);
   k_split_small<KIND, CM, 16><<<grid_small, 256, 0, st2>>>(d, level);
   k_split_small<KIND, CM, 32><<<grid_small, 256, 0, st2>>>(d, level);
   cudaEventRecord(join, st2);
@@ -1943,14 +1961,17 @@ void launch_level(const Dev& d, int level, int grid_small, int grid_items, uint6
       k_items_band<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(dc, level, -1);
     if (c + 1 == nchunks && hist_end) cudaEventRecord(hist_end, st);
     k_finalize_band<KIND, CM><<<grid_small, 256, 0, st>>>(dc, level);
+    n += 4 + (d.band_launch ? d.nbands : 1);
   }
   if (nchunks == 0) {  // grouped path
     if (hist_start) cudaEventRecord(hist_start, st);
     k_items<KIND, CM><<<grid_items, kSplitThreads, smem, st>>>(d, level);
     if (hist_end) cudaEventRecord(hist_end, st);
     k_finalize<KIND, CM><<<grid_small, 256, 0, st>>>(d, level);
+    n += 2;
   }
   cudaStreamWaitEvent(st, join, 0);
+  return n;
 }
 
 // Kernel variants: 0..4 classification with CM = 2, 3, 4, 5, 8 classes at
@@ -2004,13 +2025,12 @@ const void* small_kernel_ptr(int variant) {
   });
 }
 
-void launch_split(const Dev& d, int level, int grid_small, int grid_big, uint64_t big_bound, size_t smem,
-                  cudaStream_t st, cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hs,
-                  cudaEvent_t he) {
-  with_variant(split_variant(d.kind, d.C), [&](auto kind, auto cm) {
-    launch_level<decltype(kind)::value, decltype(cm)::value>(d, level, grid_small, grid_big, big_bound, smem, st,
-                                                              st2, fork, join, hs, he);
-    return 0;
+int launch_split(const Dev& d, int level, int grid_small, int grid_big, uint64_t big_bound, size_t smem,
+                 cudaStream_t st, cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t hs,
+                 cudaEvent_t he) {
+  return with_variant(split_variant(d.kind, d.C), [&](auto kind, auto cm) {
+    return launch_level<decltype(kind)::value, decltype(cm)::value>(d, level, grid_small, grid_big, big_bound, smem,
+                                                                     st, st2, fork, join, hs, he);
   });
 }
 

@@ -67,6 +67,9 @@ class _FakeSession:
         self.t += 1
         return 0 if self.t == 3 else 5
 
+    def kernel_launches(self):
+        return 100 + self.t  # the library's count for the step just taken
+
 
 def test_stepper_restarts_finished_runs_outside_the_step():
     import bench
@@ -80,6 +83,7 @@ def test_stepper_restarts_finished_runs_outside_the_step():
         ts.append(S.t)
     assert ts == [1, 2, 3, 1, 2, 3, 1]
     assert S.writes == 2
+    assert R.launches == sum(100 + t for t in ts)  # counted over restarts too
     R2 = bench.Stepper(_FakeSession(), max_iter=2)  # t = max_iter also ends a run
     for _ in range(3):
         R2.ready()

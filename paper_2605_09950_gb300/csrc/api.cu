@@ -266,7 +266,9 @@ static int session_init(boruta_session* s, const uint8_t* X, int64_t ld, const v
   if ((rc = s->alloc(&d.oob, MN))) return rc;
   if ((rc = s->alloc(&d.oob_cnt, n_trees))) return rc;
   if (d.permut && (rc = s->alloc(&d.piv, static_cast<size_t>(N)))) return rc;
-  if (d.permut && (rc = s->alloc(&d.Xrow, static_cast<size_t>(N) * ((p_aug_max + 15) / 16 * 16)))) return rc;
+  // the row-major copy of Xaug: the small-node split reads a row's sampled
+  // columns from it, and the Alg. 3 walks a row's path
+  if ((rc = s->alloc(&d.Xrow, static_cast<size_t>(N) * ((p_aug_max + 15) / 16 * 16)))) return rc;
   const size_t P = cap;
   if ((rc = s->alloc(&d.nd_tree, P))) return rc;
   if ((rc = s->alloc(&d.nd_heap, P))) return rc;
@@ -550,6 +552,8 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   CK_LAUNCH("k_shadow");
   nk += launch_bootstrap(d, s->tree_grid, st);
   CK_LAUNCH("bootstrap kernels");
+  nk += launch_transpose(d, s->permut_grid, st);
+  CK_LAUNCH("k_transpose_rows");
   for (int level = 0; level < d.D; ++level) {
     // grids sized to what the level can hold (every split kernel loops over
     // its work, so any grid is correct): at most M * min(2^level, N) nodes, of

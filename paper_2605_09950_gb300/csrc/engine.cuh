@@ -32,9 +32,9 @@ struct Dev {
   uint32_t* oob;                 // [M][N] out-of-bag rows, ascending
   uint32_t* oob_cnt;             // [M]
   uint32_t* piv;                 // [N] Alg. 3 flush_index of the iteration (Permut only)
-  uint8_t* Xrow;                 // [N][ldP] row-major copy of Xaug for the Alg. 3 walks (Permut only):
-                                 //   a walk reads one row's bins again and again, and a row's
-                                 //   record stays in cache where its columns would not
+  uint8_t* Xrow;                 // [N][ldP] row-major copy of Xaug, built each iteration: the
+                                 //   small-node split and the Alg. 3 walks read one row's bins
+                                 //   of many columns, which a row's record keeps together
   int32_t ldP;                   // round16(p_aug) of the iteration
   // ---- node pool (level-major; within a level, ordered by (tree, heap))
   uint32_t cap;
@@ -129,6 +129,9 @@ int launch_gather_live(const Dev& d, cudaStream_t st);
 int launch_children(const Dev& d, int level, cudaStream_t st);
 int launch_treeimp(const Dev& d, int grid, cudaStream_t st);
 int launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st);
+// Xrow (the row-major copy of Xaug): built once per iteration, after the
+// shadows, for the small-node split and the walks
+int launch_transpose(const Dev& d, int grid, cudaStream_t st);
 int launch_forest_permut(const Dev& d, int grid, cudaStream_t st);
 const void* permut_kernel_ptr(int precision);  // for its occupancy
 size_t permut_smem_bytes(int D);                // its dynamic shared memory per block (128 threads)

@@ -714,7 +714,6 @@ __global__ void k_permut_final(Dev d) {
 
 int launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
   k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
-  k_transpose_rows<<<grid, 256, 0, st>>>(d);
   k_pack_nodes<<<grid, 256, 0, st>>>(d);
   const size_t smem = 4 * permut_smem_per_warp(d.D);
   if (d.precision == 0)
@@ -722,7 +721,12 @@ int launch_permut(const Dev& d, int grid, int walk_grid, cudaStream_t st) {
   else
     k_permut<1><<<walk_grid, 128, smem, st>>>(d);
   k_permut_final<<<grid, 256, 0, st>>>(d);
-  return 5;
+  return 4;
+}
+
+int launch_transpose(const Dev& d, int grid, cudaStream_t st) {
+  k_transpose_rows<<<grid, 256, 0, st>>>(d);
+  return 1;
 }
 
 size_t permut_smem_bytes(int D) { return 4 * permut_smem_per_warp(D); }
@@ -881,11 +885,10 @@ __global__ void k_fperm_final(Dev d) {
 int launch_forest_permut(const Dev& d, int grid, cudaStream_t st) {
   int n = 0;
   k_permut_pi<<<(d.N + 255) / 256 < 1024 ? (d.N + 255) / 256 : 1024, 256, 0, st>>>(d);
-  k_transpose_rows<<<grid, 256, 0, st>>>(d);
   cudaMemsetAsync(d.fbase, 0, static_cast<size_t>(d.N) * forest_k(d) * kCsaLimbs * sizeof(long long), st);
   k_fperm_base<<<grid, 256, 0, st>>>(d);
   k_fperm_base_mean<<<grid, 256, 0, st>>>(d);
-  n += 4;
+  n += 3;
   for (uint32_t r0 = 0; r0 < static_cast<uint32_t>(d.N); r0 += d.frows) {
     const uint32_t rows = min(d.frows, static_cast<uint32_t>(d.N) - r0);
     k_fperm_delta<<<grid, 256, 0, st>>>(d, r0, rows);

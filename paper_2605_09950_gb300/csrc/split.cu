@@ -76,6 +76,13 @@ __device__ __forceinline__ const uint8_t* column(const Dev& d, uint32_t f) {
   return d.Xaug + static_cast<int64_t>(f) * d.ldN;
 }
 
+// The bin of one row and column for a node's row-by-row reads, from the
+// row-major copy: a row's sampled columns then share its few kilobytes
+// instead of lying a column apart.
+__device__ __forceinline__ uint32_t row_bin(const Dev& d, uint32_t row, uint32_t f) {
+  return d.Xrow[static_cast<int64_t>(row) * d.ldP + f];
+}
+
 // L2 residency in the histogram kernels.  The bins are gathered band by band
 // (the groups are sorted by feature band), and a band's columns must stay in
 // L2 while its groups run; the nodes' row entries, streamed once per feature
@@ -687,7 +694,7 @@ __device__ void small_node(const Dev& d, int level, uint32_t k, uint8_t* sbin, u
 #pragma unroll
       for (int u = 0; u < kSmallAhead; ++u) {
         const uint32_t fu = __shfl_sync(kFull, myf, min(j0 + u, ns - 1), SEG);
-        bv[u] = (v && j0 + u < ns) ? column(d, fu)[row] : 0u;
+        bv[u] = (v && j0 + u < ns) ? row_bin(d, row, fu) : 0u;
       }
       __syncwarp();
 #pragma unroll
@@ -708,7 +715,7 @@ __device__ void small_node(const Dev& d, int level, uint32_t k, uint8_t* sbin, u
   if (has && hl == 0) bytes += static_cast<unsigned long long>(nd.len) * (d.mtry + 4ull + (KIND ? 8ull : 0ull));
   // stable partition: left rows in order, then right rows in order
   const bool split = has && sp != kLeaf;
-  const uint32_t bs = (v && split) ? column(d, sp >> 8)[row] : 0u;
+  const uint32_t bs = (v && split) ? row_bin(d, row, sp >> 8) : 0u;
   const bool gl = v && split && bs <= (sp & 255u), gr = v && split && !gl;
   const unsigned sm = seg_mask<SEG>();
   const unsigned bl = __ballot_sync(kFull, gl) & sm, br = __ballot_sync(kFull, gr) & sm;

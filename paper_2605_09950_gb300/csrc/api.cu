@@ -521,10 +521,13 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
       dl.band_launch = 1;
     } else if (s->band_policy == 0 && level >= 0) {
       // all warps on one band at a time pays once a band's groups fill the
-      // GPU twice over; with fewer, the launches of the bands run part-empty
+      // GPU twice over (with fewer, the launches of the bands run part-empty)
+      // and while the level runs in one chunk (with several, the per-band
+      // launches multiply by the chunks and measured slower)
       const uint64_t groups_per_band = big * static_cast<uint64_t>(d.mtry) / static_cast<uint64_t>(dl.nbands);
       const uint64_t resident = static_cast<uint64_t>(s->split_grid) * (kSplitThreads / 32);
-      dl.band_launch = groups_per_band >= 2 * resident ? 1 : 0;
+      const bool one_chunk = big <= static_cast<uint64_t>(d.chunk_cap);
+      dl.band_launch = (one_chunk && groups_per_band >= 2 * resident) ? 1 : 0;
     }
   };
   set_band(d, -1, 0);

@@ -58,7 +58,7 @@ WORKLOADS = {
 # ncu capture of a whole iteration (the profile named), valid only while the
 # kernel's and its launch code's sources hash to sources_sha16
 TRAFFIC = {
-    "multiclass_N1000000_p500": {"bytes_per_launch": (585.1e9 + 63.12e9) / 20, "sources_sha16": "42996fcf50cdfd8b",
+    "multiclass_N1000000_p500": {"bytes_per_launch": (1357.6e9 + 99.59e9) / 20, "sources_sha16": "6d1b057c374029b0",
                                  "profile": "profiles/k_items_band_multiclass_N1000000_p500.md"},
 }
 

@@ -95,11 +95,13 @@ typedef struct {
                       timings and the choice).  0 (default): 48 MiB, launches as
                       band_launch says, 8192. */
   int band_launch; /* without autotune: 0 (default) = by level: one histogram launch per feature
-                      band (all warps on one band at a time) at the levels that run in one
-                      chunk of nodes and where a band holds at least twice as many (node,
-                      band) groups as the GPU runs warps at once (both counted from the
-                      level's largest possible node count), else one per chunk; 1 = one per
-                      band at every level; 2 = one per chunk at every level.  Same results. */
+                      band (all warps on one band at a time) at the levels where a band holds at
+                      least twice as many (node, band) groups as the GPU runs warps at once and
+                      that either run in one chunk of nodes or have small groups (estimated
+                      rows per node x items per band at most 1/8 of the group work; all
+                      counted from the level's largest possible node count), else one per
+                      chunk; 1 = one per band at every level; 2 = one per chunk at every
+                      level.  Same results. */
 } boruta_opts;
 
 /* Host-side, caller-allocated outputs. */

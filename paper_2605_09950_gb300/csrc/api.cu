@@ -520,14 +520,23 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
     } else if (s->band_policy == 1) {
       dl.band_launch = 1;
     } else if (s->band_policy == 0 && level >= 0) {
-      // all warps on one band at a time pays once a band's groups fill the
-      // GPU twice over (with fewer, the launches of the bands run part-empty)
-      // and while the level runs in one chunk (with several, the per-band
-      // launches multiply by the chunks and measured slower)
+      // All warps on one band at a time pays once a band's groups fill the
+      // GPU twice over (with fewer, the launches of the bands run part-empty).
+      // Over several chunks it multiplies the launches, each ending in a tail
+      // as long as its longest group, so there it is kept to levels whose
+      // groups are small (estimated rows per node x the node's items per
+      // band, at most the group work): measured faster on the deep levels of
+      // the N=1e6 multiclass workload (groups of ~60), slower on those of the
+      // SNP workload (groups of thousands).
       const uint64_t groups_per_band = big * static_cast<uint64_t>(d.mtry) / static_cast<uint64_t>(dl.nbands);
       const uint64_t resident = static_cast<uint64_t>(s->split_grid) * (kSplitThreads / 32);
       const bool one_chunk = big <= static_cast<uint64_t>(d.chunk_cap);
-      dl.band_launch = (one_chunk && groups_per_band >= 2 * resident) ? 1 : 0;
+      const uint64_t width = std::max<uint64_t>(1, big / static_cast<uint64_t>(d.M));  // nodes per tree, at most
+      const uint64_t rows = static_cast<uint64_t>(d.N) * 632 / 1000 / width;          // in-bag rows per node, about
+      const uint64_t per_band = std::max<uint64_t>(1, static_cast<uint64_t>(d.mtry) / static_cast<uint64_t>(dl.nbands));
+      const uint64_t group = std::min<uint64_t>(rows * per_band, d.group_work);
+      const bool small_groups = group * 8 <= d.group_work;
+      dl.band_launch = (groups_per_band >= 2 * resident && (one_chunk || small_groups)) ? 1 : 0;
     }
   };
   set_band(d, -1, 0);

@@ -58,7 +58,7 @@ WORKLOADS = {
 # ncu capture of a whole iteration (the profile named), valid only while the
 # kernel's and its launch code's sources hash to sources_sha16
 TRAFFIC = {
-    "multiclass_N1000000_p500": {"bytes_per_launch": (1357.6e9 + 99.59e9) / 20, "sources_sha16": "6d1b057c374029b0",
+    "multiclass_N1000000_p500": {"bytes_per_launch": (582.6e9 + 62.35e9) / 20, "sources_sha16": "c1e3b654761b17a6",
                                  "profile": "profiles/k_items_band_multiclass_N1000000_p500.md"},
 }
 

@@ -190,6 +190,10 @@ int boruta_batch_read(boruta_batch* b, int job, int8_t* decision, int32_t* hits,
                       double* shadow_max, int32_t* t);
 void boruta_batch_destroy(boruta_batch* b);
 
+/* The number of this library's kernels all jobs of the batch have launched
+ * since boruta_batch_create (the autotuner's timed iterations included). */
+int boruta_batch_kernel_launches(boruta_batch* b, int64_t* kernels);
+
 /*
  * Step-wise interface: the same computation one Boruta iteration at a time
  * (Alg. 1 loop body), for benchmarking, checkpoint/resume and inspection.

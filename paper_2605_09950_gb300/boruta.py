@@ -28,7 +28,8 @@ EXPORTS = [
     "boruta_batch_read", "boruta_batch_destroy", "boruta_session_create", "boruta_session_step",
     "boruta_session_read", "boruta_session_write", "boruta_session_dump",
     "boruta_session_kernel_stats", "boruta_session_importance_stats", "boruta_session_tuning",
-    "boruta_session_tuning_levels", "boruta_session_kernel_launches", "boruta_session_destroy",
+    "boruta_session_tuning_levels", "boruta_session_kernel_launches", "boruta_batch_kernel_launches",
+    "boruta_session_destroy",
     "boruta_philox", "boruta_perm",
     "boruta_u256_to_double", "boruta_binom_tails", "boruta_binom_tails_noalloc", "boruta_quantise",
     "boruta_last_error", "boruta_rank", "boruta_select_median", "boruta_fit_seeds",
@@ -98,6 +99,7 @@ def lib():
                                             ct.POINTER(ct.c_int32)]
         L.boruta_session_tuning_levels.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_int32), vp, vp, vp]
         L.boruta_session_kernel_launches.argtypes = [vp, ct.POINTER(ct.c_int64)]
+        L.boruta_batch_kernel_launches.argtypes = [vp, ct.POINTER(ct.c_int64)]
         L.boruta_session_destroy.argtypes = [vp]
         L.boruta_session_destroy.restype = None
         L.boruta_batch_create.argtypes = [ct.c_int, vp, vp, ct.POINTER(ct.c_void_p)]
@@ -237,6 +239,12 @@ class Batch:
         running = ct.c_int32()
         _check(lib().boruta_batch_run(self._h, iterations, ct.byref(running)))
         return running.value
+
+    def kernel_launches(self) -> int:
+        """Kernels all jobs have launched since the batch was created."""
+        n = ct.c_int64()
+        _check(lib().boruta_batch_kernel_launches(self._h, ct.byref(n)))
+        return n.value
 
     def read(self, j):
         p, max_iter = self._shapes[j]

@@ -105,7 +105,8 @@ struct boruta_session {
   double split_ms = 0.0;
   std::vector<double> level_ms, level_hist_ms;
   int split_launches = 0;
-  int64_t iter_kernels = 0;  // kernels the last enqueued iteration launched
+  int64_t iter_kernels = 0;   // kernels the last enqueued iteration launched
+  int64_t total_kernels = 0;  // kernels launched since the session was created
   double split_bytes = 0.0;
   std::vector<cudaEvent_t> hev;  // around the histogram kernel of each level
   double hist_ms = 0.0, hist_bytes = 0.0;
@@ -611,6 +612,7 @@ static int enqueue_iteration(boruta_session* s, int t, cudaStream_t st) {
   }
   CK_LAUNCH("k_stats / k_decide");
   s->iter_kernels = nk;
+  s->total_kernels += nk;
   CK(cudaMemcpyAsync(s->status_h, d.status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->state_pin, d.state, s->p, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->counters_h, d.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -1236,6 +1238,14 @@ int boruta_batch_run(boruta_batch* b, int iterations, int32_t* running) {
   int32_t still = 0;
   for (auto* s : b->ss) still += s->finished ? 0 : 1;
   if (running) *running = still;
+  return 0;
+}
+
+int boruta_batch_kernel_launches(boruta_batch* b, int64_t* kernels) {
+  if (!b) return fail(BORUTA_EINVAL, "batch is NULL");
+  int64_t n = 0;
+  for (const boruta_session* s : b->ss) n += s->total_kernels;
+  if (kernels) *kernels = n;
   return 0;
 }
 
